@@ -1,0 +1,580 @@
+/*
+ * Plain FP64 CPU oracle of the interpolation-free state-adaptive D2Q21 LBM
+ * (Coreixas & Latt, arXiv:2009.13426). TEST INFRASTRUCTURE ONLY: see the header.
+ *
+ * Written for readability against the paper, not for speed: populations are
+ * stored node-major ([node][i]), every step makes two full passes, and nothing
+ * is fused, blocked or reordered beyond the algorithm overview of Sec. IV.A.3.
+ */
+#include "alb_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* D2Q21 velocity set. The paper takes it from Zhang et al. (Fig. 1, Fig. 11,
+ * Tab. 3) without printing it; the reading used here is the rest velocity, the
+ * 4 unit axis, 4 unit diagonal, 4 axis-2, 4 diagonal-2 and 4 axis-3 velocities. */
+static const int XI[ORA_Q][2] = {
+    {0, 0},
+    {1, 0},  {0, 1},  {-1, 0},  {0, -1},
+    {1, 1},  {-1, 1}, {-1, -1}, {1, -1},
+    {2, 0},  {0, 2},  {-2, 0},  {0, -2},
+    {2, 2},  {-2, 2}, {-2, -2}, {2, -2},
+    {3, 0},  {0, 3},  {-3, 0},  {0, -3},
+};
+
+static const double D_SPACE = 2.0; /* D = 2 spatial dimensions (Sec. C.1) */
+
+struct ora_state {
+  ora_config cfg;
+  int n;
+  double *f, *g;        /* pre-collision populations [node][i] */
+  double *fs, *gs;      /* post-collision populations [node][i] */
+  signed char *Ux, *Uy; /* lattice of f, g */
+  signed char *Unx, *Uny; /* lattice selected for the next pull */
+  double *rho, *ux, *uy, *T; /* moments of f, g at the current step */
+  ora_stats stats;
+};
+
+void ora_velocities(int xi_x[ORA_Q], int xi_y[ORA_Q]) {
+  for (int i = 0; i < ORA_Q; ++i) {
+    xi_x[i] = XI[i][0];
+    xi_y[i] = XI[i][1];
+  }
+}
+
+/* Monomials of the 8-moment set (Eq. 8moments): 1, xi_a, xi_a xi_b, xi_a |xi|^2. */
+static void monomials(int i, double P[ORA_M]) {
+  const double x = XI[i][0], y = XI[i][1];
+  const double r2 = x * x + y * y;
+  P[0] = 1.0;
+  P[1] = x;
+  P[2] = y;
+  P[3] = x * x;
+  P[4] = x * y;
+  P[5] = y * y;
+  P[6] = x * r2;
+  P[7] = y * r2;
+}
+
+/* Targets of Eqs. G0_8mom..G3yaa_8mom, written in the lattice frame: the
+ * velocity is the one relative to the lattice shift, and 2E = |u|^2 + D T with
+ * D = 2 (Sec. C.1), so 2 rho u_a (E + T) = rho u_a (|u|^2 + 4T). */
+void ora_targets(double rho, double ubx, double uby, double T, double m[ORA_M]) {
+  const double E = 0.5 * (ubx * ubx + uby * uby + D_SPACE * T);
+  m[0] = rho;
+  m[1] = rho * ubx;
+  m[2] = rho * uby;
+  m[3] = rho * (ubx * ubx + T);
+  m[4] = rho * ubx * uby;
+  m[5] = rho * (uby * uby + T);
+  m[6] = 2.0 * rho * ubx * (E + T);
+  m[7] = 2.0 * rho * uby * (E + T);
+}
+
+/* p_i = exp(-(1 + lambda . P(xi_i))), the equilibrium divided by rho (Eq. exponential, a = rho). */
+static void exp_family(const double lambda[ORA_M], double p[ORA_Q]) {
+  for (int i = 0; i < ORA_Q; ++i) {
+    double P[ORA_M];
+    monomials(i, P);
+    double s = 1.0;
+    for (int k = 0; k < ORA_M; ++k) s += lambda[k] * P[k];
+    p[i] = exp(-s);
+  }
+}
+
+/* Dual objective F(lambda) = sum_i p_i + lambda . m (per unit density). Its
+ * gradient is -(G / rho) and its Hessian sum_i p_i P P^T, so Newton on G = 0 is
+ * Newton on this strictly convex function. */
+static double dual_value(const double lambda[ORA_M], const double p[ORA_Q], const double m[ORA_M]) {
+  double F = 0.0;
+  for (int i = 0; i < ORA_Q; ++i) F += p[i];
+  for (int k = 0; k < ORA_M; ++k) F += lambda[k] * m[k];
+  return F;
+}
+
+/* Cholesky solve of the symmetric positive definite system A x = b (A is 8x8). */
+static int cholesky_solve(const double A[ORA_M][ORA_M], const double b[ORA_M], double x[ORA_M]) {
+  double L[ORA_M][ORA_M];
+  memset(L, 0, sizeof(L));
+  for (int j = 0; j < ORA_M; ++j) {
+    double d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0) || !isfinite(d)) return ORA_ESINGULAR;
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < ORA_M; ++i) {
+      double s = A[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = s / L[j][j];
+    }
+  }
+  double y[ORA_M];
+  for (int i = 0; i < ORA_M; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+    y[i] = s / L[i][i];
+  }
+  for (int i = ORA_M - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < ORA_M; ++k) s -= L[k][i] * x[k];
+    x[i] = s / L[i][i];
+  }
+  return ORA_OK;
+}
+
+/* Maxwellian starting point: lambda_1 = -u/T, lambda_2aa = 1/(2T), the rest 0,
+ * and lambda_0 fixed by the normalisation sum_i p_i = 1. */
+static void maxwellian_guess(double ubx, double uby, double T, double lambda[ORA_M]) {
+  for (int k = 0; k < ORA_M; ++k) lambda[k] = 0.0;
+  lambda[1] = -ubx / T;
+  lambda[2] = -uby / T;
+  lambda[3] = 0.5 / T;
+  lambda[5] = 0.5 / T;
+  double p[ORA_Q];
+  exp_family(lambda, p); /* with lambda_0 = 0: p_i = exp(-1 - ...) */
+  double Z = 0.0;
+  for (int i = 0; i < ORA_Q; ++i) Z += p[i];
+  /* exp(-1 - lambda0 - rest) summed = 1  <=>  lambda0 = ln(Z) */
+  lambda[0] = log(Z);
+}
+
+/* Root of G(lambda) = 0 (Sec. II.C.2, App. C): Newton's method on the
+ * multipliers with the exact Jacobian, damped by backtracking on the convex
+ * dual. The paper uses Powell's hybrid method; the root is unique, so any
+ * convergent method yields the same equilibrium up to the tolerance. Stop when
+ * max_k |G_k| / rho <= tol (the paper's criterion 1e-12). */
+int ora_equilibrium(double rho, double ubx, double uby, double T, double tol, int maxit,
+                    double lambda[ORA_M], double feq[ORA_Q], int* iters) {
+  *iters = 0;
+  if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ubx) ||
+      !isfinite(uby))
+    return ORA_EUNREALIZABLE;
+  double m[ORA_M], mt[ORA_M];
+  ora_targets(rho, ubx, uby, T, mt);
+  for (int k = 0; k < ORA_M; ++k) m[k] = mt[k] / rho;
+
+  maxwellian_guess(ubx, uby, T, lambda);
+  double p[ORA_Q];
+  exp_family(lambda, p);
+  double F = dual_value(lambda, p, m);
+  int status = ORA_ENEWTON;
+  int it = 0;
+  for (;;) {
+    /* residual G / rho */
+    double G[ORA_M];
+    for (int k = 0; k < ORA_M; ++k) G[k] = -m[k];
+    for (int i = 0; i < ORA_Q; ++i) {
+      double P[ORA_M];
+      monomials(i, P);
+      for (int k = 0; k < ORA_M; ++k) G[k] += p[i] * P[k];
+    }
+    double gmax = 0.0;
+    for (int k = 0; k < ORA_M; ++k) gmax = fmax(gmax, fabs(G[k]));
+    if (!isfinite(gmax)) { status = ORA_ESINGULAR; break; }
+    if (gmax <= tol) { status = ORA_OK; break; }
+    if (it >= maxit) { status = ORA_ENEWTON; break; }
+    /* Jacobian dG/d(-lambda) = sum_i p_i P P^T */
+    double H[ORA_M][ORA_M];
+    memset(H, 0, sizeof(H));
+    for (int i = 0; i < ORA_Q; ++i) {
+      double P[ORA_M];
+      monomials(i, P);
+      for (int a = 0; a < ORA_M; ++a)
+        for (int b = 0; b < ORA_M; ++b) H[a][b] += p[i] * P[a] * P[b];
+    }
+    double d[ORA_M];
+    if (cholesky_solve((const double(*)[ORA_M])H, G, d) != ORA_OK) { status = ORA_ESINGULAR; break; }
+    double gd = 0.0;
+    for (int k = 0; k < ORA_M; ++k) gd += G[k] * d[k];
+    /* backtracking (Armijo) on F along lambda + t d */
+    double t = 1.0, lam_c[ORA_M], p_c[ORA_Q], F_c = 0.0;
+    int accepted = 0;
+    for (int ls = 0; ls < 40; ++ls) {
+      for (int k = 0; k < ORA_M; ++k) lam_c[k] = lambda[k] + t * d[k];
+      exp_family(lam_c, p_c);
+      F_c = dual_value(lam_c, p_c, m);
+      if (isfinite(F_c) && F_c <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = 1; break; }
+      t *= 0.5;
+    }
+    ++it;
+    if (!accepted) { status = ORA_ENEWTON; break; }
+    for (int k = 0; k < ORA_M; ++k) lambda[k] = lam_c[k];
+    for (int i = 0; i < ORA_Q; ++i) p[i] = p_c[i];
+    F = F_c;
+  }
+  *iters = it;
+  for (int i = 0; i < ORA_Q; ++i) feq[i] = rho * p[i];
+  return status;
+}
+
+/* Eq. criterion: U_a = n iff n - 0.5 < u_a <= n + 0.5. With an offset n0 the
+ * interval is read as (n - n0, n + 1 - n0]; shifts are clamped to [-umax, umax]. */
+int ora_select_shift(double u, double n0, int umax) {
+  for (int n = -umax; n <= umax; ++n) {
+    const double lo = (double)n - n0;
+    const double hi = (double)(n + 1) - n0;
+    if (lo < u && u <= hi) return n;
+  }
+  return u > 0.0 ? umax : -umax;
+}
+
+/* Eq. polyTemp, evaluated with the populations' own velocities c_i = xi_i + U:
+ * rho = sum f, rho u = sum f c, and T = [sum(|c|^2 f + g) - rho |u|^2] / (2 rho Cv).
+ * Summing in the lattice frame (xi instead of c) gives the same T exactly in
+ * exact arithmetic; the lattice frame is used so that results do not depend on U. */
+void ora_node_moments(const double f[ORA_Q], const double g[ORA_Q], int Ux, int Uy,
+                      double gamma, double out[4]) {
+  const double Cv = 1.0 / (gamma - 1.0);
+  double rho = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
+  for (int i = 0; i < ORA_Q; ++i) {
+    const double x = XI[i][0], y = XI[i][1];
+    rho += f[i];
+    jx += f[i] * x;
+    jy += f[i] * y;
+    e += (x * x + y * y) * f[i] + g[i];
+  }
+  const double ubx = jx / rho, uby = jy / rho;
+  const double T = (e - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * Cv);
+  out[0] = rho;
+  out[1] = ubx + (double)Ux;
+  out[2] = uby + (double)Uy;
+  out[3] = T;
+}
+
+/* alpha(eps_Kn): piecewise constant, 1 below the first threshold (Sec. IV.A.2;
+ * the function itself is not given in the paper). */
+static double sensor_alpha(const ora_config* c, double eps) {
+  double a = 1.0;
+  for (int k = 0; k < 3; ++k)
+    if (eps > c->sensor_eps[k]) a = c->sensor_alpha[k];
+  return a;
+}
+
+/* Collision of one node (Eqs. coll, gEq, DeltaAvg) in its own lattice U. */
+int ora_collide_node(const ora_config* cfg, const double f[ORA_Q], const double g[ORA_Q],
+                     int Ux, int Uy, double fs[ORA_Q], double gs[ORA_Q]) {
+  double mom[4];
+  ora_node_moments(f, g, Ux, Uy, cfg->gamma, mom);
+  const double rho = mom[0], T = mom[3];
+  double lambda[ORA_M], feq[ORA_Q];
+  int iters;
+  int st = ora_equilibrium(rho, mom[1] - Ux, mom[2] - Uy, T, cfg->newton_tol, cfg->newton_maxit,
+                           lambda, feq, &iters);
+  if (st != ORA_OK) {
+    /* failure policy: the node is left uncollided */
+    for (int i = 0; i < ORA_Q; ++i) { fs[i] = f[i]; gs[i] = g[i]; }
+    return st;
+  }
+  const double Cv = 1.0 / (cfg->gamma - 1.0);
+  double tau = 0.5 + cfg->nu / T;
+  if (cfg->sensor) {
+    double eps = 0.0;
+    for (int i = 0; i < ORA_Q; ++i) eps += fabs(f[i] - feq[i]) / feq[i];
+    eps /= (double)ORA_Q;
+    tau *= sensor_alpha(cfg, eps);
+  }
+  for (int i = 0; i < ORA_Q; ++i) {
+    const double geq = (2.0 * Cv - D_SPACE) * T * feq[i];
+    fs[i] = f[i] - (f[i] - feq[i]) / tau;
+    gs[i] = g[i] - (g[i] - geq) / tau;
+  }
+  return ORA_OK;
+}
+
+/* Grad's approximation h = h^eq (1 + omega phi_h): Eq. GradGeneral with phi_f
+ * from Eq. GradGeneral_f (traceless viscous stress, Fourier heat flux, mu = rho nu,
+ * kappa = rho Cp nu for Pr = 1) and phi_g from Eq. GradGeneral_g, both as printed.
+ * cbar = c_i - u with c_i = xi_i + U. */
+int ora_grad_populations(const ora_config* cfg, int Ux, int Uy, double rho, double ux,
+                         double uy, double T, const double du[2][2], const double dT[2],
+                         double omega, double f[ORA_Q], double g[ORA_Q]) {
+  const double Cv = 1.0 / (cfg->gamma - 1.0);
+  const double Cp = cfg->gamma * Cv;
+  double lambda[ORA_M], feq[ORA_Q];
+  int iters;
+  int st = ora_equilibrium(rho, ux - Ux, uy - Uy, T, cfg->newton_tol, cfg->newton_maxit, lambda,
+                           feq, &iters);
+  if (st != ORA_OK) return st;
+  const double mu = rho * cfg->nu;
+  const double kappa = rho * Cp * cfg->nu;
+  /* -sigma_ab = mu [d_a u_b + d_b u_a - (2/D) d_c u_c delta_ab] */
+  const double div = du[0][0] + du[1][1];
+  const double sxx = -mu * (2.0 * du[0][0] - (2.0 / D_SPACE) * div);
+  const double syy = -mu * (2.0 * du[1][1] - (2.0 / D_SPACE) * div);
+  const double sxy = -mu * (du[0][1] + du[1][0]);
+  const double qx = -kappa * dT[0];
+  const double qy = -kappa * dT[1];
+  for (int i = 0; i < ORA_Q; ++i) {
+    const double cx = (double)(XI[i][0] + Ux) - ux;
+    const double cy = (double)(XI[i][1] + Uy) - uy;
+    const double c2 = cx * cx + cy * cy;
+    const double qc = qx * cx + qy * cy;
+    const double phi_f = (sxx * cx * cx + 2.0 * sxy * cx * cy + syy * cy * cy) / (2.0 * rho * T * T) +
+                         qc / (rho * Cp * T * T) * (c2 / (2.0 * T) - Cp);
+    const double phi_g = 2.0 * qc / (rho * Cp);
+    const double geq = (2.0 * Cv - D_SPACE) * T * feq[i];
+    f[i] = feq[i] * (1.0 + omega * phi_f);
+    g[i] = geq * (1.0 + omega * phi_g);
+  }
+  return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Grid helpers */
+
+/* Resolve a coordinate along one axis: periodic wrap, or, for zero-gradient
+ * ends, clamp into the domain (ghost nodes carry the nearest interior moments).
+ * *ghost is set when the coordinate was outside the domain. */
+static int resolve(int x, int n, int bc, int* ghost) {
+  if (bc == ORA_PERIODIC) {
+    int r = x % n;
+    if (r < 0) r += n;
+    *ghost = 0;
+    return r;
+  }
+  if (x < 0) { *ghost = 1; return 0; }
+  if (x >= n) { *ghost = 1; return n - 1; }
+  *ghost = 0;
+  return x;
+}
+
+/* Second-order central differences of a node field at (x, y), x and y possibly
+ * ghost coordinates (Sec. IV.A.1: gradients by second-order FD). Neighbours are
+ * resolved with the boundary rule, so a gradient across a zero-gradient end is 0. */
+static void central_diff(const ora_state* s, const double* F, int x, int y, double d[2]) {
+  const int nx = s->cfg.nx, ny = s->cfg.ny;
+  int gh;
+  const int ry = resolve(y, ny, s->cfg.bc_y, &gh);
+  const int rx = resolve(x, nx, s->cfg.bc_x, &gh);
+  const int xp = resolve(x + 1, nx, s->cfg.bc_x, &gh);
+  const int xm = resolve(x - 1, nx, s->cfg.bc_x, &gh);
+  const int yp = resolve(y + 1, ny, s->cfg.bc_y, &gh);
+  const int ym = resolve(y - 1, ny, s->cfg.bc_y, &gh);
+  d[0] = 0.5 * (F[ry * nx + xp] - F[ry * nx + xm]);
+  d[1] = 0.5 * (F[yp * nx + rx] - F[ym * nx + rx]);
+}
+
+ora_state* ora_create(const ora_config* cfg) {
+  if (cfg->nx <= 0 || cfg->ny <= 0 || cfg->umax < 0 || cfg->umax > 3) return NULL;
+  ora_state* s = (ora_state*)calloc(1, sizeof(ora_state));
+  if (!s) return NULL;
+  s->cfg = *cfg;
+  s->n = cfg->nx * cfg->ny;
+  const size_t nq = (size_t)s->n * ORA_Q;
+  s->f = (double*)calloc(nq, sizeof(double));
+  s->g = (double*)calloc(nq, sizeof(double));
+  s->fs = (double*)calloc(nq, sizeof(double));
+  s->gs = (double*)calloc(nq, sizeof(double));
+  s->Ux = (signed char*)calloc(s->n, 1);
+  s->Uy = (signed char*)calloc(s->n, 1);
+  s->Unx = (signed char*)calloc(s->n, 1);
+  s->Uny = (signed char*)calloc(s->n, 1);
+  s->rho = (double*)calloc(s->n, sizeof(double));
+  s->ux = (double*)calloc(s->n, sizeof(double));
+  s->uy = (double*)calloc(s->n, sizeof(double));
+  s->T = (double*)calloc(s->n, sizeof(double));
+  if (!s->f || !s->g || !s->fs || !s->gs || !s->Ux || !s->Uy || !s->Unx || !s->Uny || !s->rho ||
+      !s->ux || !s->uy || !s->T) {
+    ora_destroy(s);
+    return NULL;
+  }
+  return s;
+}
+
+void ora_destroy(ora_state* s) {
+  if (!s) return;
+  free(s->f); free(s->g); free(s->fs); free(s->gs);
+  free(s->Ux); free(s->Uy); free(s->Unx); free(s->Uny);
+  free(s->rho); free(s->ux); free(s->uy); free(s->T);
+  free(s);
+}
+
+/* Initial condition (Sec. IV.A.1, IV.B): populations h = h^eq (1 + phi_h) from
+ * the given fields, in the lattice chosen by the criterion for the initial
+ * velocity, with FD gradients of the initial u and T. */
+int ora_init(ora_state* s, const double* rho, const double* rhoux, const double* rhouy,
+             const double* rhoE) {
+  const ora_config* c = &s->cfg;
+  const int nx = c->nx, ny = c->ny;
+  const double Cv = 1.0 / (c->gamma - 1.0);
+  for (int k = 0; k < s->n; ++k) {
+    const double r = rho[k];
+    if (!(r > 0.0)) return ORA_EUNREALIZABLE;
+    const double ux = rhoux[k] / r, uy = rhouy[k] / r;
+    const double T = (rhoE[k] - 0.5 * r * (ux * ux + uy * uy)) / (r * Cv);
+    if (!(T > 0.0)) return ORA_EUNREALIZABLE;
+    s->rho[k] = r; s->ux[k] = ux; s->uy[k] = uy; s->T[k] = T;
+  }
+  memset(&s->stats, 0, sizeof(s->stats));
+  int status = ORA_OK;
+  for (int y = 0; y < ny; ++y) {
+    for (int x = 0; x < nx; ++x) {
+      const int k = y * nx + x;
+      const int Ux = ora_select_shift(s->ux[k], c->n0, c->umax);
+      const int Uy = ora_select_shift(s->uy[k], c->n0, c->umax);
+      double du[2][2], dT[2], dux[2], duy[2];
+      central_diff(s, s->ux, x, y, dux);
+      central_diff(s, s->uy, x, y, duy);
+      central_diff(s, s->T, x, y, dT);
+      du[0][0] = dux[0]; du[1][0] = dux[1]; /* du[a][b] = d_a u_b */
+      du[0][1] = duy[0]; du[1][1] = duy[1];
+      int st = ora_grad_populations(c, Ux, Uy, s->rho[k], s->ux[k], s->uy[k], s->T[k], du, dT,
+                                    1.0, &s->f[(size_t)k * ORA_Q], &s->g[(size_t)k * ORA_Q]);
+      if (st != ORA_OK) status = st;
+      s->Ux[k] = (signed char)Ux;
+      s->Uy[k] = (signed char)Uy;
+    }
+  }
+  return status;
+}
+
+/* Post-collision population of velocity i pulled by a node in lattice (Upx, Upy)
+ * from the (possibly ghost) sender (sx, sy) whose lattice differs: Grad rebuild
+ * with the sender's moments and gradients and the sender's relaxation time. */
+static int rebuild_pull(ora_state* s, int i, int Upx, int Upy, int sx, int sy, double* fi,
+                        double* gi) {
+  const ora_config* c = &s->cfg;
+  int gx, gy;
+  const int rx = resolve(sx, c->nx, c->bc_x, &gx);
+  const int ry = resolve(sy, c->ny, c->bc_y, &gy);
+  const int k = ry * c->nx + rx;
+  double dux[2], duy[2], dT[2], du[2][2];
+  central_diff(s, s->ux, sx, sy, dux);
+  central_diff(s, s->uy, sx, sy, duy);
+  central_diff(s, s->T, sx, sy, dT);
+  du[0][0] = dux[0]; du[1][0] = dux[1];
+  du[0][1] = duy[0]; du[1][1] = duy[1];
+  const double tau = 0.5 + c->nu / s->T[k];
+  double f[ORA_Q], g[ORA_Q];
+  int st = ora_grad_populations(c, Upx, Upy, s->rho[k], s->ux[k], s->uy[k], s->T[k], du, dT,
+                                1.0 - 1.0 / tau, f, g);
+  if (st != ORA_OK) return st;
+  *fi = f[i];
+  *gi = g[i];
+  return ORA_OK;
+}
+
+/* Fallback for a rebuild whose root finder failed: the Maxwellian-guess
+ * exponential (always positive) of the sender's state in the receiver's lattice. */
+static void rebuild_fallback(ora_state* s, int i, int Upx, int Upy, int sx, int sy, double* fi,
+                             double* gi) {
+  const ora_config* c = &s->cfg;
+  int gx, gy;
+  const int k = resolve(sy, c->ny, c->bc_y, &gy) * c->nx + resolve(sx, c->nx, c->bc_x, &gx);
+  const double Cv = 1.0 / (c->gamma - 1.0);
+  double lambda[ORA_M], p[ORA_Q];
+  maxwellian_guess(s->ux[k] - Upx, s->uy[k] - Upy, s->T[k], lambda);
+  exp_family(lambda, p);
+  *fi = s->rho[k] * p[i];
+  *gi = (2.0 * Cv - D_SPACE) * s->T[k] * (*fi);
+}
+
+int ora_step(ora_state* s, int nsteps) {
+  const ora_config* c = &s->cfg;
+  const int nx = c->nx, ny = c->ny;
+  int status = ORA_OK;
+  for (int step = 0; step < nsteps; ++step) {
+    /* (i) moments, equilibrium, collision, next shift: every node in its own lattice */
+    long long fails = 0, calls = 0;
+#pragma omp parallel for reduction(+ : fails, calls) schedule(static)
+    for (int k = 0; k < s->n; ++k) {
+      const double* f = &s->f[(size_t)k * ORA_Q];
+      const double* g = &s->g[(size_t)k * ORA_Q];
+      double mom[4];
+      ora_node_moments(f, g, s->Ux[k], s->Uy[k], c->gamma, mom);
+      s->rho[k] = mom[0]; s->ux[k] = mom[1]; s->uy[k] = mom[2]; s->T[k] = mom[3];
+      int st = ora_collide_node(c, f, g, s->Ux[k], s->Uy[k], &s->fs[(size_t)k * ORA_Q],
+                                &s->gs[(size_t)k * ORA_Q]);
+      calls += 1;
+      if (st != ORA_OK) fails += 1;
+      s->Unx[k] = (signed char)ora_select_shift(mom[1], c->n0, c->umax);
+      s->Uny[k] = (signed char)ora_select_shift(mom[2], c->n0, c->umax);
+    }
+    s->stats.newton_calls += calls;
+    s->stats.newton_failures += fails;
+    if (fails) status = ORA_ENEWTON;
+
+    /* (ii) pull streaming in the receiver's new lattice, Grad rebuild of missing pulls */
+    long long rec = 0, rec_fail = 0;
+#pragma omp parallel for reduction(+ : rec, rec_fail) schedule(static)
+    for (int k = 0; k < s->n; ++k) {
+      const int x = k % nx, y = k / nx;
+      const int Upx = s->Unx[k], Upy = s->Uny[k];
+      for (int i = 0; i < ORA_Q; ++i) {
+        const int sx = x - (XI[i][0] + Upx);
+        const int sy = y - (XI[i][1] + Upy);
+        int gx, gy;
+        const int rx = resolve(sx, nx, c->bc_x, &gx);
+        const int ry = resolve(sy, ny, c->bc_y, &gy);
+        const int ks = ry * nx + rx;
+        double fi, gi;
+        if (!gx && !gy && s->Ux[ks] == Upx && s->Uy[ks] == Upy) {
+          fi = s->fs[(size_t)ks * ORA_Q + i];
+          gi = s->gs[(size_t)ks * ORA_Q + i];
+        } else {
+          rec += 1;
+          if (rebuild_pull(s, i, Upx, Upy, sx, sy, &fi, &gi) != ORA_OK) {
+            rec_fail += 1;
+            rebuild_fallback(s, i, Upx, Upy, sx, sy, &fi, &gi);
+          }
+        }
+        s->f[(size_t)k * ORA_Q + i] = fi;
+        s->g[(size_t)k * ORA_Q + i] = gi;
+      }
+    }
+    s->stats.reconstructions += rec;
+    s->stats.reconstruction_failures += rec_fail;
+    if (rec_fail) status = ORA_ENEWTON;
+
+    /* (iii) the received populations now live in the new lattice */
+    memcpy(s->Ux, s->Unx, (size_t)s->n);
+    memcpy(s->Uy, s->Uny, (size_t)s->n);
+  }
+  return status;
+}
+
+void ora_get_primitives(const ora_state* s, double* rho, double* ux, double* uy, double* T) {
+  for (int k = 0; k < s->n; ++k) {
+    double mom[4];
+    ora_node_moments(&s->f[(size_t)k * ORA_Q], &s->g[(size_t)k * ORA_Q], s->Ux[k], s->Uy[k],
+                     s->cfg.gamma, mom);
+    rho[k] = mom[0]; ux[k] = mom[1]; uy[k] = mom[2]; T[k] = mom[3];
+  }
+}
+
+void ora_get_moments(const ora_state* s, double* rho, double* rhoux, double* rhouy,
+                     double* rhoE) {
+  const double Cv = 1.0 / (s->cfg.gamma - 1.0);
+  for (int k = 0; k < s->n; ++k) {
+    double mom[4];
+    ora_node_moments(&s->f[(size_t)k * ORA_Q], &s->g[(size_t)k * ORA_Q], s->Ux[k], s->Uy[k],
+                     s->cfg.gamma, mom);
+    const double r = mom[0], ux = mom[1], uy = mom[2], T = mom[3];
+    rho[k] = r;
+    rhoux[k] = r * ux;
+    rhouy[k] = r * uy;
+    rhoE[k] = 0.5 * r * (ux * ux + uy * uy) + r * Cv * T;
+  }
+}
+
+void ora_get_shifts(const ora_state* s, signed char* ux, signed char* uy) {
+  memcpy(ux, s->Ux, (size_t)s->n);
+  memcpy(uy, s->Uy, (size_t)s->n);
+}
+
+void ora_get_populations(const ora_state* s, double* f, double* g) {
+  memcpy(f, s->f, sizeof(double) * (size_t)s->n * ORA_Q);
+  memcpy(g, s->g, sizeof(double) * (size_t)s->n * ORA_Q);
+}
+
+void ora_set_state(ora_state* s, const double* f, const double* g, const signed char* ux,
+                   const signed char* uy) {
+  memcpy(s->f, f, sizeof(double) * (size_t)s->n * ORA_Q);
+  memcpy(s->g, g, sizeof(double) * (size_t)s->n * ORA_Q);
+  memcpy(s->Ux, ux, (size_t)s->n);
+  memcpy(s->Uy, uy, (size_t)s->n);
+}
+
+void ora_get_stats(const ora_state* s, ora_stats* out) { *out = s->stats; }

@@ -1,0 +1,130 @@
+/*
+ * Plain FP64 CPU oracle of the interpolation-free state-adaptive D2Q21 lattice
+ * Boltzmann method (Coreixas & Latt, arXiv:2009.13426).
+ *
+ * TEST INFRASTRUCTURE ONLY. This code is the slow, obviously-correct reference
+ * that the CUDA path is checked against. Only the test-suite, the smoke check
+ * and the benchmark's CPU-baseline leg may load it. The product library never
+ * links, loads or calls it, and it shares no code with the CUDA path.
+ *
+ * Everything is double precision. One time step is two full passes over the
+ * grid, in the order of the algorithm overview of Sec. IV.A.3:
+ *   (i)  per node: moments (Eq. polyTemp), numerical equilibrium (Eq. feqNum_8Mom
+ *        with the 8 constraints G0_8mom..G3yaa_8mom), g^eq (Eq. gEq), optional
+ *        kinetic sensor (Eq. DeltaAvg), BGK collision (Eq. coll), and the shift
+ *        U' for the next pull (Eq. criterion);
+ *   (ii) per node and velocity: pull streaming (Eq. stream) from x - (xi_i + U'(x));
+ *        a pull whose sender lives in another lattice is rebuilt by Grad's
+ *        reconstruction (Eqs. GradGeneral, GradGeneral_f, GradGeneral_g) with
+ *        second-order central differences of u and T at the sender.
+ *
+ * Parity status of each function is given beside it and in the repository's
+ * design notes.
+ */
+#ifndef ALB_ORACLE_H
+#define ALB_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORA_Q 21   /* D2Q21 */
+#define ORA_M 8    /* 8-moment constraint set */
+
+enum { ORA_PERIODIC = 0, ORA_ZERO_GRADIENT = 1 };
+
+enum {
+  ORA_OK = 0,
+  ORA_ENEWTON = 1,       /* root finder did not reach the tolerance */
+  ORA_ESINGULAR = 2,     /* Jacobian not positive definite / non-finite values */
+  ORA_EUNREALIZABLE = 3, /* rho <= 0 or T <= 0 */
+  ORA_EINVAL = 4
+};
+
+typedef struct {
+  int nx, ny;
+  int umax;            /* shift set {-umax..umax}^2 */
+  double nu;           /* kinematic viscosity (lattice units) */
+  double gamma;        /* specific heat ratio gamma_r */
+  double n0;           /* criterion offset: U = n iff n - n0 < u <= n + 1 - n0 */
+  int bc_x, bc_y;      /* ORA_PERIODIC | ORA_ZERO_GRADIENT */
+  int sensor;          /* 1: tau <- tau * alpha(eps_Kn) (Eq. DeltaAvg) */
+  double sensor_eps[3];   /* increasing thresholds of eps_Kn */
+  double sensor_alpha[3]; /* alpha applied above each threshold */
+  double newton_tol;   /* max_k |G_k| / rho */
+  int newton_maxit;
+} ora_config;
+
+typedef struct {
+  long long newton_calls;
+  long long newton_iters;
+  long long newton_failures;      /* node equilibria that failed (node not collided) */
+  long long reconstructions;      /* missing pulls rebuilt by Grad's formula */
+  long long reconstruction_failures;
+} ora_stats;
+
+typedef struct ora_state ora_state;
+
+/* Velocity table, index order used everywhere in the oracle. */
+void ora_velocities(int xi_x[ORA_Q], int xi_y[ORA_Q]);
+
+/* Numerical equilibrium (Eqs. exponential, feqNum_8Mom) in a lattice whose
+ * populations move with xi_i + U: (rho, ubx, uby) is the velocity relative to U.
+ * Writes the 8 multipliers (order: 0, x, y, xx, xy, yy, x|xi|^2, y|xi|^2) and
+ * f^eq_i. Returns ORA_OK or an error code; *iters receives the Newton count. */
+int ora_equilibrium(double rho, double ubx, double uby, double T, double tol,
+                    int maxit, double lambda[ORA_M], double feq[ORA_Q], int* iters);
+
+/* Constraint targets M_k(rho, ubar, T) of Eqs. G0_8mom..G3yaa_8mom. */
+void ora_targets(double rho, double ubx, double uby, double T, double m[ORA_M]);
+
+/* Shift criterion (Eq. criterion, with the n0 offset reading). */
+int ora_select_shift(double u, double n0, int umax);
+
+/* Macroscopic moments of one node (Eq. polyTemp), populations in lattice U.
+ * out = {rho, ux, uy, T} with u absolute (lattice-frame sums plus U). */
+void ora_node_moments(const double f[ORA_Q], const double g[ORA_Q], int Ux, int Uy,
+                      double gamma, double out[4]);
+
+/* BGK collision of one node in its own lattice (Eqs. coll, gEq; optional
+ * sensor). Returns ORA_OK or a Newton error (then fs, gs = f, g). */
+int ora_collide_node(const ora_config* cfg, const double f[ORA_Q], const double g[ORA_Q],
+                     int Ux, int Uy, double fs[ORA_Q], double gs[ORA_Q]);
+
+/* Grad populations h = h^eq (1 + omega * phi_h) in lattice (Ux, Uy) for the
+ * macroscopic state (rho, ux, uy, T) with velocity gradients du[a][b] = d_a u_b
+ * and temperature gradient dT[a] (Eqs. GradGeneral, GradGeneral_f, _g).
+ * omega = 1 for initial conditions, 1 - 1/tau for post-collision rebuilds. */
+int ora_grad_populations(const ora_config* cfg, int Ux, int Uy, double rho, double ux,
+                         double uy, double T, const double du[2][2], const double dT[2],
+                         double omega, double f[ORA_Q], double g[ORA_Q]);
+
+ora_state* ora_create(const ora_config* cfg);
+void ora_destroy(ora_state* s);
+
+/* Grad-regularised initial state from conserved fields (x fastest, nx*ny each):
+ * rho, rho*ux, rho*uy, rho*E with rho*E = rho|u|^2/2 + rho*Cv*T. */
+int ora_init(ora_state* s, const double* rho, const double* rhoux, const double* rhouy,
+             const double* rhoE);
+
+/* Advance nsteps time iterations. Returns ORA_OK, or ORA_ENEWTON if any node
+ * failed (state stays valid, failures are counted). */
+int ora_step(ora_state* s, int nsteps);
+
+/* Conserved moments of the current (pre-collision) populations. */
+void ora_get_moments(const ora_state* s, double* rho, double* rhoux, double* rhouy,
+                     double* rhoE);
+/* Primitive moments (rho, ux, uy, T) of the current populations. */
+void ora_get_primitives(const ora_state* s, double* rho, double* ux, double* uy, double* T);
+/* Lattice of the current populations. */
+void ora_get_shifts(const ora_state* s, signed char* ux, signed char* uy);
+/* Populations, layout [node][i]. */
+void ora_get_populations(const ora_state* s, double* f, double* g);
+void ora_set_state(ora_state* s, const double* f, const double* g, const signed char* ux,
+                   const signed char* uy);
+void ora_get_stats(const ora_state* s, ora_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,213 @@
+"""Pins of the oracle's numerical equilibrium against what the paper and the
+mathematics fix, independently of the oracle's own code:
+
+* the velocity set (reading of Fig. 1 / Tab. 3) as a set;
+* the constraint targets of Eqs. G0_8mom..G3yaa_8mom are the moments of the
+  continuous Maxwellian (checked by Gauss-Hermite quadrature);
+* at rest the equilibrium has the closed form rho exp(-a|xi|^2)/Z, with a the
+  root of a scalar equation (bisection here);
+* away from rest the result is the unique maximiser of the entropy: it lies in
+  the exponential family of Eq. exponential and meets the constraints, and a
+  generic optimiser (scipy BFGS on the dual) finds the same point;
+* the residual criterion 1e-12 gives constraint errors near 1e-14 (App. C.1);
+* the operability edge u_x ~ 2 printed in Sec. III.A.2 (golden file) and an
+  LP feasibility test of the moment vector agree with convergence.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# Velocity set of the D2Q21 lattice as read from the paper (rest, axis 1,
+# diagonal 1, axis 2, diagonal 2, axis 3).
+D2Q21 = {(0, 0)}
+for a in (1, -1):
+    D2Q21 |= {(a, 0), (0, a), (2 * a, 0), (0, 2 * a), (3 * a, 0), (0, 3 * a)}
+    for b in (1, -1):
+        D2Q21 |= {(a, b), (2 * a, 2 * b)}
+
+
+def _xi():
+    x, y = O.velocities()
+    return x.astype(np.float64), y.astype(np.float64)
+
+
+def _monomials(x, y):
+    r2 = x * x + y * y
+    return np.stack([np.ones_like(x), x, y, x * x, x * y, y * y, x * r2, y * r2])
+
+
+def test_velocity_set_is_d2q21():
+    x, y = O.velocities()
+    pts = list(zip(x.tolist(), y.tolist()))
+    assert len(pts) == 21 and len(set(pts)) == 21
+    assert set(pts) == D2Q21
+    assert pts[0] == (0, 0)
+
+
+@pytest.mark.parametrize("ubx,uby,T", [(0.0, 0.0, 0.7), (0.3, -0.2, 0.5), (-0.45, 0.4, 1.1),
+                                        (1.2, 0.1, 0.8)])
+def test_targets_are_maxwellian_moments(ubx, uby, T):
+    # Gauss-Hermite (probabilists') quadrature is exact for these polynomials.
+    z, w = np.polynomial.hermite_e.hermegauss(12)
+    w = w / w.sum()
+    X = ubx + math.sqrt(T) * z[:, None]
+    Y = uby + math.sqrt(T) * z[None, :]
+    W = w[:, None] * w[None, :]
+    P = _monomials(np.broadcast_to(X, W.shape), np.broadcast_to(Y, W.shape))
+    rho = 1.3
+    expect = rho * (P * W).sum(axis=(1, 2))
+    got = O.targets(rho, ubx, uby, T)
+    np.testing.assert_allclose(got, expect, rtol=1e-13, atol=1e-13)
+
+
+def _rest_parameter(T):
+    """a such that sum_i xi_x^2 e^{-a|xi|^2} / sum_i e^{-a|xi|^2} = T, by bisection."""
+    pts = np.array(sorted(D2Q21), dtype=np.float64)
+    r2 = (pts ** 2).sum(axis=1)
+
+    def var(a):
+        w = np.exp(-a * r2)
+        return float((w * pts[:, 0] ** 2).sum() / w.sum())
+
+    lo, hi = 1e-6, 50.0  # var decreases with a
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if var(mid) > T:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("T", [0.4, 0.7, 1.0, 1.3])
+def test_rest_state_closed_form(T):
+    rho = 0.9
+    st, lam, feq, _ = O.equilibrium(rho, 0.0, 0.0, T)
+    assert st == O.OK
+    a = _rest_parameter(T)
+    x, y = _xi()
+    w = np.exp(-a * (x * x + y * y))
+    np.testing.assert_allclose(feq, rho * w / w.sum(), rtol=1e-12, atol=0)
+    # multipliers: lambda_1 = lambda_2xy = lambda_3 = 0, lambda_2xx = lambda_2yy = a
+    np.testing.assert_allclose(lam[[1, 2, 4, 6, 7]], 0.0, atol=1e-11)
+    np.testing.assert_allclose(lam[[3, 5]], a, rtol=1e-10)
+
+
+def _states(n, seed, umax=0.75):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        r = rng.uniform(0.1, 3.0)
+        ang = rng.uniform(0, 2 * math.pi)
+        mag = rng.uniform(0, umax)
+        T = rng.uniform(0.4, 1.3)
+        out.append((r, mag * math.cos(ang), mag * math.sin(ang), T))
+    return out
+
+
+@pytest.mark.parametrize("state", _states(12, 7))
+def test_equilibrium_is_the_constrained_exponential(state):
+    rho, ubx, uby, T = state
+    st, lam, feq, its = O.equilibrium(rho, ubx, uby, T)
+    assert st == O.OK
+    x, y = _xi()
+    P = _monomials(x, y)
+    # constraints (Eqs. G0_8mom..G3yaa_8mom), targets from the Maxwellian moments
+    E = 0.5 * (ubx * ubx + uby * uby + 2 * T)
+    M = np.array([rho, rho * ubx, rho * uby, rho * (ubx ** 2 + T), rho * ubx * uby,
+                  rho * (uby ** 2 + T), 2 * rho * ubx * (E + T), 2 * rho * uby * (E + T)])
+    np.testing.assert_allclose(P @ feq, M, rtol=0, atol=1e-12 * rho * 30)
+    # exponential family (Eq. exponential with a = rho): -1 - ln(f/rho) in span{P}
+    rhs = -1.0 - np.log(feq / rho)
+    coef, *_ = np.linalg.lstsq(P.T, rhs, rcond=None)
+    assert np.abs(P.T @ coef - rhs).max() < 1e-10
+    np.testing.assert_allclose(coef, lam, rtol=1e-8, atol=1e-8)
+
+
+@pytest.mark.parametrize("state", _states(5, 11))
+def test_equilibrium_matches_generic_optimiser(state):
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    rho, ubx, uby, T = state
+    st, lam, feq, _ = O.equilibrium(rho, ubx, uby, T)
+    assert st == O.OK
+    x, y = _xi()
+    P = _monomials(x, y)
+    E = 0.5 * (ubx * ubx + uby * uby + 2 * T)
+    m = np.array([1, ubx, uby, ubx ** 2 + T, ubx * uby, uby ** 2 + T, 2 * ubx * (E + T),
+                  2 * uby * (E + T)])
+
+    def F(l):
+        p = np.exp(-1.0 - l @ P)
+        return p.sum() + l @ m, m - P @ p
+
+    l0 = np.zeros(8)
+    l0[3] = l0[5] = 0.5 / T
+    res = scipy_opt.minimize(F, l0, jac=True, method="BFGS", options={"gtol": 1e-13, "maxiter": 5000})
+    f_opt = rho * np.exp(-1.0 - res.x @ P)
+    np.testing.assert_allclose(feq, f_opt, rtol=1e-7, atol=1e-12)
+
+
+def test_residual_reaches_machine_precision():
+    """Criterion 1e-12 leaves constraint errors around 1e-14 (App. C.1)."""
+    x, y = _xi()
+    P = _monomials(x, y)
+    errs = []
+    iters = []
+    for rho, ubx, uby, T in _states(200, 3):
+        st, lam, feq, its = O.equilibrium(rho, ubx, uby, T)
+        assert st == O.OK
+        mt = O.targets(rho, ubx, uby, T)
+        errs.append(np.abs(P @ feq - mt).max() / rho)
+        iters.append(its)
+    errs = np.array(errs)
+    assert errs.max() <= 1e-12
+    assert np.median(errs) < 1e-13
+    assert max(iters) <= 15
+
+
+def _golden_edge():
+    rows = []
+    with open(os.path.join(GOLDEN, "realizability_edge.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(float(v) for v in line.split()))
+    return rows
+
+
+@pytest.mark.parametrize("T,u_ok,u_bad", _golden_edge())
+def test_operability_edge_printed_in_paper(T, u_ok, u_bad):
+    st, *_ = O.equilibrium(1.0, u_ok, 0.0, T, maxit=100)
+    assert st == O.OK
+    st, *_ = O.equilibrium(1.0, u_bad, 0.0, T, maxit=100)
+    assert st != O.OK
+
+
+def test_reference_temperature_golden():
+    with open(os.path.join(GOLDEN, "reference_temperature.txt")) as fh:
+        vals = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    T0 = float(dict(vals)["Q21"])
+    st, lam, feq, _ = O.equilibrium(1.0, 0.0, 0.0, T0)
+    assert st == O.OK and T0 == 0.7
+
+
+@pytest.mark.parametrize("u,T", [(0.5, 0.7), (1.2, 0.7), (1.6, 0.6), (1.8, 0.5), (2.05, 0.7),
+                                 (2.3, 0.6), (3.0, 0.7), (1.0, 0.2), (0.5, 0.22)])
+def test_lp_feasibility_agrees_with_convergence(u, T):
+    """The moment vector is realisable by positive populations iff the LP
+    {f >= eps : sum f P = M} is feasible; the root finder converges exactly then
+    (away from the edge)."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    x, y = _xi()
+    P = _monomials(x, y)
+    m = O.targets(1.0, u, 0.0, T)
+    lp = scipy_opt.linprog(np.zeros(21), A_eq=P, b_eq=m, bounds=[(1e-7, None)] * 21,
+                           method="highs")
+    feasible = lp.status == 0
+    st, *_ = O.equilibrium(1.0, u, 0.0, T, maxit=200)
+    assert feasible == (st == O.OK)
