@@ -243,13 +243,21 @@ void ora_node_moments(const double f[ORA_Q], const double g[ORA_Q], int Ux, int 
   out[3] = T;
 }
 
-/* alpha(eps_Kn): piecewise constant, 1 below the first threshold (Sec. IV.A.2;
- * the function itself is not given in the paper). */
+/* alpha(eps_Kn) of Sec. IV.A.2. The paper gives only its onset (alpha = 1 for
+ * eps_Kn <= 0.01); the function itself comes from another work. Reading used
+ * here: continuous and piecewise linear in log10(eps) through the knots
+ * (e0, 1), (e1, a0), (e2, a1), (10 e2, a2), constant beyond, so that the
+ * relaxation time is a continuous function of the populations. */
 static double sensor_alpha(const ora_config* c, double eps) {
-  double a = 1.0;
+  const double* e = c->sensor_eps;
+  const double* a = c->sensor_alpha;
+  if (!(eps > e[0])) return 1.0;
+  const double kx[4] = {log10(e[0]), log10(e[1]), log10(e[2]), log10(e[2]) + 1.0};
+  const double ky[4] = {1.0, a[0], a[1], a[2]};
+  const double l = log10(eps);
   for (int k = 0; k < 3; ++k)
-    if (eps > c->sensor_eps[k]) a = c->sensor_alpha[k];
-  return a;
+    if (l <= kx[k + 1]) return ky[k] + (ky[k + 1] - ky[k]) * (l - kx[k]) / (kx[k + 1] - kx[k]);
+  return a[2];
 }
 
 /* Collision of one node (Eqs. coll, gEq, DeltaAvg) in its own lattice U. */

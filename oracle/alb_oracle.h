@@ -49,8 +49,8 @@ typedef struct {
   double n0;           /* criterion offset: U = n iff n - n0 < u <= n + 1 - n0 */
   int bc_x, bc_y;      /* ORA_PERIODIC | ORA_ZERO_GRADIENT */
   int sensor;          /* 1: tau <- tau * alpha(eps_Kn) (Eq. DeltaAvg) */
-  double sensor_eps[3];   /* increasing thresholds of eps_Kn */
-  double sensor_alpha[3]; /* alpha applied above each threshold */
+  double sensor_eps[3];   /* increasing knots e0 < e1 < e2 of eps_Kn */
+  double sensor_alpha[3]; /* alpha at e1, e2 and 10 e2 (alpha = 1 up to e0) */
   double newton_tol;   /* max_k |G_k| / rho */
   int newton_maxit;
 } ora_config;

@@ -1,0 +1,262 @@
+"""Thin Python binding of the C ABI in include/alb.h (libalb.so).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. The functions keep the C names. Host arrays are numpy float64
+(or int8) arrays; device arrays are torch CUDA tensors (torch is used for
+device memory and streams only). There is no CPU fallback: if libalb.so is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libalb.so")
+
+ALB_OK = 0
+ALB_EINVAL = -1
+ALB_ENOMEM = -2
+ALB_EUNSUPPORTED = -3
+ALB_ENEWTON = -4
+ALB_EUNREALIZABLE = -5
+ALB_ETIMEDOUT = -6
+ALB_EBUSY = -7
+ALB_ECUDA = -8
+ALB_ENOTFOUND = -9
+
+ALB_D2Q21 = 21
+ALB_FP64_PLAIN = 0
+ALB_FP32_FORM = 1
+ALB_PERIODIC = 0
+ALB_ZERO_GRADIENT = 1
+ALB_HOST = 0
+ALB_DEVICE = 1
+Q = 21
+
+
+class AlbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("alb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class alb_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("stencil", ctypes.c_int),
+        ("u_max", ctypes.c_int), ("nu", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("n0", ctypes.c_double), ("precision", ctypes.c_int), ("bc_x", ctypes.c_int),
+        ("bc_y", ctypes.c_int), ("sensor", ctypes.c_int),
+        ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
+        ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class alb_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "steps", "node_updates", "newton_iterations", "newton_failures", "reconstructions",
+        "reconstruction_failures")]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "alb_config_default": (ctypes.c_int, [ctypes.POINTER(alb_config)]),
+    "alb_create": (ctypes.c_int, [ctypes.POINTER(alb_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "alb_init": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]),
+    "alb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "alb_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "alb_moments": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]),
+    "alb_shifts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "alb_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(alb_stats)]),
+    "alb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "alb_last_error": (ctypes.c_char_p, []),
+    "alb_equilibrium": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_double,
+                                                                ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "alb_select_shift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "alb_velocities": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libalb.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libalb.so not built: run `python -c \"import __graft_entry__ as g; "
+                               "g.build()\"` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return sorted(_SIGS)
+
+
+def alb_last_error() -> str:
+    return lib().alb_last_error().decode()
+
+
+def _check(rc):
+    if rc != ALB_OK:
+        raise AlbError(rc, alb_last_error())
+    return rc
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected numpy array or torch tensor, got %r" % type(a))
+
+
+def _where(a):
+    return ALB_DEVICE if (hasattr(a, "is_cuda") and a.is_cuda) else ALB_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def alb_config_default(**kw) -> alb_config:
+    c = alb_config()
+    _check(lib().alb_config_default(ctypes.byref(c)))
+    for k, v in kw.items():
+        if k in ("sensor_eps", "sensor_alpha"):
+            arr = getattr(c, k)
+            for j in range(3):
+                arr[j] = v[j]
+        elif k == "stream":
+            c.stream = _stream(v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def alb_create(cfg: alb_config):
+    h = ctypes.c_void_p()
+    _check(lib().alb_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def alb_init(h, rho, rhoux, rhouy, rhoE):
+    where = _where(rho)
+    arrs = [rho, rhoux, rhouy, rhoE]
+    if where == ALB_HOST:
+        arrs = [np.ascontiguousarray(a, np.float64) for a in arrs]
+    return _check(lib().alb_init(h, *[_ptr(a) for a in arrs], where))
+
+
+def alb_step(h, nsteps: int):
+    return _check(lib().alb_step(h, int(nsteps)))
+
+
+def alb_sync(h, timeout_ms: int = -1):
+    return _check(lib().alb_sync(h, int(timeout_ms)))
+
+
+def alb_moments(h, out):
+    """out: 4 arrays (numpy float64 or torch float64 CUDA tensors) of nx*ny."""
+    return _check(lib().alb_moments(h, *[_ptr(a) for a in out], _where(out[0])))
+
+
+def alb_shifts(h, ux, uy):
+    return _check(lib().alb_shifts(h, _ptr(ux), _ptr(uy), _where(ux)))
+
+
+def alb_stats_get(h) -> dict:
+    s = alb_stats()
+    _check(lib().alb_stats_get(h, ctypes.byref(s)))
+    return {k: int(getattr(s, k)) for k, _ in alb_stats._fields_}
+
+
+def alb_destroy(h):
+    return _check(lib().alb_destroy(h))
+
+
+def alb_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lam=None, iters=None, status=None,
+                    stream=None):
+    """All arrays are torch CUDA tensors (float64; iters/status int32)."""
+    return _check(lib().alb_equilibrium(_ptr(rho), _ptr(ubx), _ptr(uby), _ptr(T), int(n),
+                                        float(tol), int(maxit), _ptr(feq), _ptr(lam), _ptr(iters),
+                                        _ptr(status), _stream(stream)))
+
+
+def alb_select_shift(rho, rhou, n, n0, u_max, out, stream=None):
+    return _check(lib().alb_select_shift(_ptr(rho), _ptr(rhou), int(n), float(n0), int(u_max),
+                                         _ptr(out), _stream(stream)))
+
+
+def alb_velocities():
+    x = np.zeros(Q, np.int32)
+    y = np.zeros(Q, np.int32)
+    _check(lib().alb_velocities(x.ctypes.data, y.ctypes.data))
+    return x, y
+
+
+class Flow:
+    """One flow on the GPU (owns an alb_handle). Fields are (ny, nx) arrays."""
+
+    def __init__(self, nx, ny, **cfg):
+        self.cfg = alb_config_default(nx=nx, ny=ny, **cfg)
+        self.nx, self.ny = nx, ny
+        self.h = alb_create(self.cfg)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            alb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, rhoux, rhouy, rhoE):
+        return alb_init(self.h, rho, rhoux, rhouy, rhoE)
+
+    def step(self, n):
+        return alb_step(self.h, n)
+
+    def sync(self, timeout_ms=-1):
+        return alb_sync(self.h, timeout_ms)
+
+    def moments(self):
+        n = self.nx * self.ny
+        out = [np.empty(n) for _ in range(4)]
+        alb_moments(self.h, out)
+        return [a.reshape(self.ny, self.nx) for a in out]
+
+    def shifts(self):
+        n = self.nx * self.ny
+        ux = np.empty(n, np.int8)
+        uy = np.empty(n, np.int8)
+        alb_shifts(self.h, ux, uy)
+        return ux.reshape(self.ny, self.nx), uy.reshape(self.ny, self.nx)
+
+    def stats(self):
+        return alb_stats_get(self.h)

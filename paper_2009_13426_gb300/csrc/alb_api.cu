@@ -1,0 +1,350 @@
+// C ABI of the single-flow path (include/alb.h): configuration checks, device
+// allocation, stream handling, host/device staging, error reporting.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "../../include/alb.h"
+#include "alb_internal.h"
+
+using namespace alb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(ALB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ALB_CUDA(call, what)                      \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+}  // namespace
+
+struct alb_handle {
+  alb_config cfg;
+  FlowDev dev;
+  cudaStream_t stream;
+  bool own_stream;
+  double* staging;        // 4 * n doubles for host transfers
+  unsigned long long* ctr_host;
+  uint64_t steps;
+  bool initialised;
+};
+
+extern "C" {
+
+const char* alb_last_error(void) { return g_err; }
+
+int alb_velocities(int* xi_x, int* xi_y) {
+  if (!xi_x || !xi_y) return fail(ALB_EINVAL, "alb_velocities: null pointer");
+  for (int i = 0; i < Q; ++i) {
+    xi_x[i] = XI_X(i);
+    xi_y[i] = XI_Y(i);
+  }
+  return ALB_OK;
+}
+
+int alb_config_default(alb_config* c) {
+  if (!c) return fail(ALB_EINVAL, "alb_config_default: null pointer");
+  memset(c, 0, sizeof(*c));
+  c->nx = 64;
+  c->ny = 64;
+  c->stencil = ALB_D2Q21;
+  c->u_max = 2;
+  c->nu = 1e-3;
+  c->gamma = 1.4;
+  c->n0 = 0.5;
+  c->precision = ALB_FP64_PLAIN;
+  c->bc_x = ALB_PERIODIC;
+  c->bc_y = ALB_PERIODIC;
+  c->sensor = 0;
+  c->sensor_eps[0] = 0.01;
+  c->sensor_eps[1] = 0.1;
+  c->sensor_eps[2] = 1.0;
+  c->sensor_alpha[0] = 1.05;
+  c->sensor_alpha[1] = 1.35;
+  c->sensor_alpha[2] = 1.6;
+  c->newton_tol = 1e-12;
+  c->newton_maxit = 50;
+  c->stream = nullptr;
+  return ALB_OK;
+}
+
+static int check_config(const alb_config* c) {
+  if (!c) return fail(ALB_EINVAL, "null config");
+  if (c->stencil != ALB_D2Q21) return fail(ALB_EUNSUPPORTED, "only ALB_D2Q21 is supported");
+  if (c->nx < 1 || c->ny < 1) return fail(ALB_EINVAL, "grid %d x %d is empty", c->nx, c->ny);
+  if ((long long)c->nx * c->ny > (1LL << 31)) return fail(ALB_EINVAL, "grid too large");
+  if (c->ny > 65535) return fail(ALB_EINVAL, "ny must be <= 65535");
+  if (c->u_max < 0 || c->u_max > 3) return fail(ALB_EINVAL, "u_max must be in [0, 3]");
+  if (!(c->nu >= 0.0)) return fail(ALB_EINVAL, "nu must be >= 0");
+  if (!(c->gamma > 1.0)) return fail(ALB_EINVAL, "gamma must be > 1");
+  if (!(c->n0 > 0.0 && c->n0 < 1.0)) return fail(ALB_EINVAL, "n0 must be in (0, 1)");
+  if (c->precision != ALB_FP64_PLAIN && c->precision != ALB_FP32_FORM)
+    return fail(ALB_EINVAL, "unknown precision %d", c->precision);
+  if ((c->bc_x != ALB_PERIODIC && c->bc_x != ALB_ZERO_GRADIENT) ||
+      (c->bc_y != ALB_PERIODIC && c->bc_y != ALB_ZERO_GRADIENT))
+    return fail(ALB_EINVAL, "unknown boundary kind");
+  if (c->sensor && !(c->sensor_eps[0] > 0.0 && c->sensor_eps[0] < c->sensor_eps[1] &&
+                     c->sensor_eps[1] < c->sensor_eps[2]))
+    return fail(ALB_EINVAL, "sensor_eps must be positive and increasing");
+  if (!(c->newton_tol > 0.0) || c->newton_maxit < 1)
+    return fail(ALB_EINVAL, "newton_tol must be > 0 and newton_maxit >= 1");
+  return ALB_OK;
+}
+
+int alb_destroy(alb_handle* h) {
+  if (!h) return ALB_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->dev.pop[b]);
+    cudaFree(h->dev.mom[b]);
+    cudaFree(h->dev.lat[b]);
+    cudaFree(h->dev.nxt[b]);
+  }
+  cudaFree(h->dev.ctr);
+  cudaFree(h->staging);
+  cudaFreeHost(h->ctr_host);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return ALB_OK;
+}
+
+int alb_create(const alb_config* cfg, alb_handle** out) {
+  if (!out) return fail(ALB_EINVAL, "alb_create: null output");
+  *out = nullptr;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  alb_handle* h = new (std::nothrow) alb_handle();
+  if (!h) return fail(ALB_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  FlowDev& d = h->dev;
+  Params& p = d.prm;
+  p.nx = cfg->nx;
+  p.ny = cfg->ny;
+  p.umax = cfg->u_max;
+  p.bcx = cfg->bc_x;
+  p.bcy = cfg->bc_y;
+  p.sensor = cfg->sensor;
+  p.maxit = cfg->newton_maxit;
+  p.nu = cfg->nu;
+  p.gamma = cfg->gamma;
+  p.n0 = cfg->n0;
+  p.tol = cfg->newton_tol;
+  p.cv = 1.0 / (cfg->gamma - 1.0);
+  p.cp = cfg->gamma * p.cv;
+  for (int j = 0; j < 3; ++j) {
+    p.seps[j] = cfg->sensor_eps[j];
+    p.salpha[j] = cfg->sensor_alpha[j];
+  }
+  p.skx[0] = log10(cfg->sensor_eps[0]);
+  p.skx[1] = log10(cfg->sensor_eps[1]);
+  p.skx[2] = log10(cfg->sensor_eps[2]);
+  p.skx[3] = p.skx[2] + 1.0;
+  p.sky[0] = 1.0;
+  p.sky[1] = cfg->sensor_alpha[0];
+  p.sky[2] = cfg->sensor_alpha[1];
+  p.sky[3] = cfg->sensor_alpha[2];
+  d.precision = cfg->precision;
+  d.n = (size_t)cfg->nx * cfg->ny;
+  d.ps = (d.n + 63) / 64 * 64;
+  d.cur = 0;
+  const size_t es = d.precision == ALB_FP64_PLAIN ? sizeof(double) : sizeof(float);
+  if (cfg->stream) {
+    h->stream = (cudaStream_t)cfg->stream;
+    h->own_stream = false;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    h->own_stream = true;
+  }
+#define ALLOC(ptr, bytes)                                              \
+  do {                                                                 \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));              \
+    if (e_ != cudaSuccess) {                                           \
+      alb_destroy(h);                                                  \
+      cudaGetLastError();                                              \
+      return fail(ALB_ENOMEM, "cudaMalloc of %zu bytes failed: %s", (size_t)(bytes), \
+                  cudaGetErrorString(e_));                             \
+    }                                                                  \
+  } while (0)
+  for (int b = 0; b < 2; ++b) {
+    ALLOC(d.pop[b], NPLANES * d.ps * es);
+    ALLOC(d.mom[b], 4 * d.ps * es);
+    ALLOC(d.lat[b], d.ps);
+    ALLOC(d.nxt[b], d.ps);
+  }
+  ALLOC(d.ctr, CTR_COUNT * sizeof(unsigned long long));
+  ALLOC(h->staging, 4 * d.n * sizeof(double));
+#undef ALLOC
+  if (cudaMallocHost((void**)&h->ctr_host, CTR_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
+    alb_destroy(h);
+    return fail(ALB_ENOMEM, "pinned host allocation failed");
+  }
+  *out = h;
+  return ALB_OK;
+}
+
+int alb_init(alb_handle* h, const double* rho, const double* rhoux, const double* rhouy,
+             const double* rhoE, int where) {
+  if (!h || !rho || !rhoux || !rhouy || !rhoE) return fail(ALB_EINVAL, "alb_init: null pointer");
+  const size_t n = h->dev.n;
+  const double *r = rho, *a = rhoux, *b = rhouy, *e = rhoE;
+  ALB_CUDA(cudaMemsetAsync(h->dev.ctr, 0, CTR_COUNT * sizeof(unsigned long long), h->stream),
+           "alb_init: counter reset");
+  if (where == ALB_HOST) {
+    double* s = h->staging;
+    ALB_CUDA(cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "H2D");
+    ALB_CUDA(cudaMemcpyAsync(s + n, rhoux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+             "H2D");
+    ALB_CUDA(cudaMemcpyAsync(s + 2 * n, rhouy, n * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream), "H2D");
+    ALB_CUDA(cudaMemcpyAsync(s + 3 * n, rhoE, n * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream), "H2D");
+    r = s; a = s + n; b = s + 2 * n; e = s + 3 * n;
+  } else if (where != ALB_DEVICE) {
+    return fail(ALB_EINVAL, "alb_init: where must be ALB_HOST or ALB_DEVICE");
+  }
+  h->dev.cur = 0;
+  ALB_CUDA(launch_init(h->dev, r, a, b, e, h->stream), "alb_init: init kernel");
+  ALB_CUDA(cudaMemcpyAsync(h->ctr_host, h->dev.ctr, CTR_COUNT * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->stream), "alb_init: counters");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_init: synchronise");
+  h->steps = 0;
+  h->initialised = true;
+  if (h->ctr_host[CTR_UNREALIZABLE])
+    return fail(ALB_EUNREALIZABLE, "alb_init: %llu nodes with rho <= 0 or T <= 0",
+                h->ctr_host[CTR_UNREALIZABLE]);
+  if (h->ctr_host[CTR_NEWTON_FAIL])
+    return fail(ALB_ENEWTON, "alb_init: %llu nodes without a converged equilibrium",
+                h->ctr_host[CTR_NEWTON_FAIL]);
+  return ALB_OK;
+}
+
+int alb_step(alb_handle* h, int nsteps) {
+  if (!h) return fail(ALB_EINVAL, "alb_step: null handle");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_step: call alb_init first");
+  if (nsteps < 0) return fail(ALB_EINVAL, "alb_step: nsteps < 0");
+  for (int s = 0; s < nsteps; ++s)
+    ALB_CUDA(launch_step(h->dev, h->stream), "alb_step: step kernel");
+  h->steps += (uint64_t)nsteps;
+  return ALB_OK;
+}
+
+int alb_sync(alb_handle* h, int timeout_ms) {
+  if (!h) return fail(ALB_EINVAL, "alb_sync: null handle");
+  ALB_CUDA(cudaMemcpyAsync(h->ctr_host, h->dev.ctr, CTR_COUNT * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->stream), "alb_sync: counters");
+  if (timeout_ms < 0) {
+    ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_sync");
+  } else {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      cudaError_t e = cudaStreamQuery(h->stream);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return cuda_fail(e, "alb_sync");
+      auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                    std::chrono::steady_clock::now() - t0).count();
+      if (ms >= timeout_ms) return fail(ALB_ETIMEDOUT, "alb_sync: still running after %d ms", timeout_ms);
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+  }
+  if (h->ctr_host[CTR_NEWTON_FAIL] || h->ctr_host[CTR_REC_FAIL])
+    return fail(ALB_ENEWTON, "%llu node equilibria and %llu rebuilds failed",
+                h->ctr_host[CTR_NEWTON_FAIL], h->ctr_host[CTR_REC_FAIL]);
+  return ALB_OK;
+}
+
+int alb_moments(alb_handle* h, double* rho, double* rhoux, double* rhouy, double* rhoE,
+                int where) {
+  if (!h || !rho || !rhoux || !rhouy || !rhoE) return fail(ALB_EINVAL, "alb_moments: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_moments: call alb_init first");
+  const size_t n = h->dev.n;
+  if (where == ALB_DEVICE) {
+    ALB_CUDA(launch_export_moments(h->dev, rho, rhoux, rhouy, rhoE, h->stream), "alb_moments");
+    return ALB_OK;
+  }
+  if (where != ALB_HOST) return fail(ALB_EINVAL, "alb_moments: bad where");
+  double* s = h->staging;
+  ALB_CUDA(launch_export_moments(h->dev, s, s + n, s + 2 * n, s + 3 * n, h->stream), "alb_moments");
+  double* outs[4] = {rho, rhoux, rhouy, rhoE};
+  for (int j = 0; j < 4; ++j)
+    ALB_CUDA(cudaMemcpyAsync(outs[j], s + j * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream), "alb_moments: D2H");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_moments: synchronise");
+  return ALB_OK;
+}
+
+int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where) {
+  if (!h || !ux || !uy) return fail(ALB_EINVAL, "alb_shifts: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_shifts: call alb_init first");
+  const size_t n = h->dev.n;
+  if (where == ALB_DEVICE) {
+    ALB_CUDA(launch_export_shifts(h->dev, ux, uy, h->stream), "alb_shifts");
+    return ALB_OK;
+  }
+  if (where != ALB_HOST) return fail(ALB_EINVAL, "alb_shifts: bad where");
+  signed char* s = (signed char*)h->staging;
+  ALB_CUDA(launch_export_shifts(h->dev, s, s + n, h->stream), "alb_shifts");
+  ALB_CUDA(cudaMemcpyAsync(ux, s, n, cudaMemcpyDeviceToHost, h->stream), "alb_shifts: D2H");
+  ALB_CUDA(cudaMemcpyAsync(uy, s + n, n, cudaMemcpyDeviceToHost, h->stream), "alb_shifts: D2H");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_shifts: synchronise");
+  return ALB_OK;
+}
+
+int alb_stats_get(alb_handle* h, alb_stats* out) {
+  if (!h || !out) return fail(ALB_EINVAL, "alb_stats_get: null pointer");
+  ALB_CUDA(cudaMemcpyAsync(h->ctr_host, h->dev.ctr, CTR_COUNT * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->stream), "alb_stats_get");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_stats_get: synchronise");
+  out->steps = h->steps;
+  out->node_updates = h->steps * (uint64_t)h->dev.n;
+  out->newton_iterations = h->ctr_host[CTR_NEWTON_ITERS];
+  out->newton_failures = h->ctr_host[CTR_NEWTON_FAIL];
+  out->reconstructions = h->ctr_host[CTR_REC];
+  out->reconstruction_failures = h->ctr_host[CTR_REC_FAIL];
+  return ALB_OK;
+}
+
+int alb_equilibrium(const double* rho, const double* ubx, const double* uby, const double* T,
+                    int n, double tol, int maxit, double* feq, double* lambda, int* iters,
+                    int* status, void* stream) {
+  if (n < 0 || (n > 0 && (!rho || !ubx || !uby || !T || !feq)))
+    return fail(ALB_EINVAL, "alb_equilibrium: bad arguments");
+  if (!(tol > 0.0) || maxit < 1) return fail(ALB_EINVAL, "alb_equilibrium: bad tolerance");
+  ALB_CUDA(launch_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lambda, iters, status,
+                              (cudaStream_t)stream), "alb_equilibrium");
+  return ALB_OK;
+}
+
+int alb_select_shift(const double* rho, const double* rhou, int n, double n0, int u_max,
+                     signed char* out, void* stream) {
+  if (n < 0 || (n > 0 && (!rho || !rhou || !out)))
+    return fail(ALB_EINVAL, "alb_select_shift: bad arguments");
+  if (u_max < 0 || u_max > 3 || !(n0 > 0.0 && n0 < 1.0))
+    return fail(ALB_EINVAL, "alb_select_shift: bad u_max or n0");
+  ALB_CUDA(launch_select(rho, rhou, n, n0, u_max, out, (cudaStream_t)stream), "alb_select_shift");
+  return ALB_OK;
+}
+
+}  // extern "C"

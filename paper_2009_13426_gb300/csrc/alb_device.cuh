@@ -1,0 +1,300 @@
+// Device-side building blocks of the adaptive D2Q21 LBM step (sm_103a).
+//
+// The lattice, the 8-moment numerical equilibrium and its FP64 Newton solve,
+// the shift criterion and Grad's reconstruction, written for one node per
+// thread. Loops over velocities are fully unrolled with compile-time velocity
+// components, so every multiplication by a zero component disappears and the
+// sums below touch only the velocities that contribute.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace alb {
+
+constexpr int Q = 21;   // D2Q21
+constexpr int NM = 8;   // 8-moment constraint set (Eq. 8moments)
+constexpr int NPLANES = 2 * Q;  // f and g planes
+
+// D2Q21 velocity set (Fig. 1 / Tab. 3 reading): rest, axis 1, diagonal 1,
+// axis 2, diagonal 2, axis 3. The index order is part of the C ABI
+// (alb_velocities, alb_equilibrium).
+__host__ __device__ __forceinline__ constexpr int XI_X(int i) {
+  return i == 1 ? 1 : i == 3 ? -1 : i == 5 ? 1 : i == 6 ? -1 : i == 7 ? -1 : i == 8 ? 1
+       : i == 9 ? 2 : i == 11 ? -2 : i == 13 ? 2 : i == 14 ? -2 : i == 15 ? -2 : i == 16 ? 2
+       : i == 17 ? 3 : i == 19 ? -3 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int XI_Y(int i) {
+  return i == 2 ? 1 : i == 4 ? -1 : i == 5 ? 1 : i == 6 ? 1 : i == 7 ? -1 : i == 8 ? -1
+       : i == 10 ? 2 : i == 12 ? -2 : i == 13 ? 2 : i == 14 ? 2 : i == 15 ? -2 : i == 16 ? -2
+       : i == 18 ? 3 : i == 20 ? -3 : 0;
+}
+// Monomial k of the 8-moment set at velocity i: 1, x, y, x^2, xy, y^2, x|xi|^2, y|xi|^2.
+__host__ __device__ __forceinline__ constexpr int PM(int k, int i) {
+  return k == 0 ? 1 : k == 1 ? XI_X(i) : k == 2 ? XI_Y(i) : k == 3 ? XI_X(i) * XI_X(i)
+       : k == 4 ? XI_X(i) * XI_Y(i) : k == 5 ? XI_Y(i) * XI_Y(i)
+       : k == 6 ? XI_X(i) * (XI_X(i) * XI_X(i) + XI_Y(i) * XI_Y(i))
+       : XI_Y(i) * (XI_X(i) * XI_X(i) + XI_Y(i) * XI_Y(i));
+}
+
+// Lattice code of a shift U in [-3, 3]^2: one byte per node.
+__host__ __device__ __forceinline__ int lat_code(int ux, int uy) { return (ux + 3) + 7 * (uy + 3); }
+__host__ __device__ __forceinline__ int lat_ux(int c) { return c % 7 - 3; }
+__host__ __device__ __forceinline__ int lat_uy(int c) { return c / 7 - 3; }
+
+// Physical and numerical parameters of one flow, passed by value.
+struct Params {
+  int nx, ny;
+  int umax;
+  int bcx, bcy;      // 0 periodic, 1 zero-gradient
+  int sensor;
+  int maxit;
+  double nu, gamma, n0, tol;
+  double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
+  double seps[3], salpha[3];
+  double skx[4], sky[4];  // sensor knots: log10(eps) and alpha (host-computed)
+};
+
+// s + c * v with c a compile-time integer after unrolling: the zero and unit
+// cases fold away, keeping IEEE semantics for the rest.
+template <typename R>
+__device__ __forceinline__ R madd(R s, R v, int c) {
+  if (c == 0) return s;
+  if (c == 1) return s + v;
+  if (c == -1) return s - v;
+  return fma(v, (R)c, s);
+}
+
+// Eq. criterion with offset n0: U = n iff n - n0 < u <= n + 1 - n0, clamped.
+__device__ __forceinline__ int select_shift(double u, double n0, int umax) {
+  int n = -umax;
+  // count the thresholds n + 1 - n0 (n = -umax .. umax-1) that u lies above
+  for (int t = -umax; t < umax; ++t) {
+    const double hi = (double)(t + 1) - n0;
+    if (u > hi) n = t + 1;
+  }
+  return n;
+}
+
+// alpha(eps_Kn) of the kinetic sensor (Sec. IV.A.2): 1 up to seps[0], then
+// continuous and piecewise linear in log10(eps) through (seps[1], salpha[0]),
+// (seps[2], salpha[1]), (10 seps[2], salpha[2]), constant beyond. Evaluated
+// in the population precision P.
+template <typename P>
+__device__ __forceinline__ P sensor_alpha(const Params& pr, P eps) {
+  if (!(eps > (P)pr.seps[0])) return (P)1;
+  const P l = log10(eps);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (l <= (P)pr.skx[k + 1])
+      return (P)pr.sky[k] + ((P)pr.sky[k + 1] - (P)pr.sky[k]) * (l - (P)pr.skx[k]) /
+                                ((P)pr.skx[k + 1] - (P)pr.skx[k]);
+  return (P)pr.sky[3];
+}
+
+// Targets of Eqs. G0_8mom..G3yaa_8mom per unit density, lattice frame.
+__device__ __forceinline__ void targets(double ubx, double uby, double T, double m[NM]) {
+  const double u2 = ubx * ubx + uby * uby;
+  m[0] = 1.0;
+  m[1] = ubx;
+  m[2] = uby;
+  m[3] = ubx * ubx + T;
+  m[4] = ubx * uby;
+  m[5] = uby * uby + T;
+  m[6] = ubx * (u2 + 4.0 * T);
+  m[7] = uby * (u2 + 4.0 * T);
+}
+
+// p_i = exp(-(1 + lambda . P(xi_i))) for all 21 velocities (Eq. exponential / rho).
+__device__ __forceinline__ void exp_family(const double lam[NM], double p[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    double s = 1.0 + lam[0];
+#pragma unroll
+    for (int k = 1; k < NM; ++k) s = madd(s, lam[k], PM(k, i));
+    p[i] = exp(-s);
+  }
+}
+
+__device__ __forceinline__ double dual_value(const double lam[NM], const double p[Q],
+                                             const double m[NM]) {
+  double F = 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) F += p[i];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) F = fma(lam[k], m[k], F);
+  return F;
+}
+
+enum { NEWTON_OK = 0, NEWTON_MAXIT = 1, NEWTON_SINGULAR = 2, NEWTON_UNREALIZABLE = 3 };
+
+// Maxwellian starting multipliers, lambda_0 from the normalisation sum p = 1.
+__device__ __forceinline__ void maxwellian_guess(double ubx, double uby, double T, double lam[NM]) {
+  const double iT = 1.0 / T;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) lam[k] = 0.0;
+  lam[1] = -ubx * iT;
+  lam[2] = -uby * iT;
+  lam[3] = 0.5 * iT;
+  lam[5] = 0.5 * iT;
+  double p[Q];
+  exp_family(lam, p);
+  double Z = 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Z += p[i];
+  lam[0] = log(Z);
+}
+
+// FP64 Newton on the multipliers of the 8-moment equilibrium (Sec. II.C.2,
+// App. C), damped by backtracking on the strictly convex dual
+// F(lambda) = sum_i p_i + lambda . m, whose gradient is -G/rho and Hessian the
+// exact Jacobian sum_i p_i P P^T. Stops at max_k |G_k|/rho <= tol. On return p
+// holds the equilibrium per unit density at lam.
+static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T, double tol, int maxit,
+                                        double lam[NM], double p[Q], int* iters) {
+  *iters = 0;
+  if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
+  double m[NM];
+  targets(ubx, uby, T, m);
+  maxwellian_guess(ubx, uby, T, lam);
+  exp_family(lam, p);
+  double F = dual_value(lam, p, m);
+  int it = 0;
+  for (;;) {
+    double G[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      double s = -m[k];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) s = madd(s, p[i], PM(k, i));
+      G[k] = s;
+    }
+    double gmax = 0.0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) gmax = fmax(gmax, fabs(G[k]));
+    if (!isfinite(gmax)) { *iters = it; return NEWTON_SINGULAR; }
+    if (gmax <= tol) { *iters = it; return NEWTON_OK; }
+    if (it >= maxit) { *iters = it; return NEWTON_MAXIT; }
+    // Jacobian (lower triangle), then in-place Cholesky factor
+    double H[NM][NM];
+#pragma unroll
+    for (int a = 0; a < NM; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s = madd(s, p[i], PM(a, i) * PM(b, i));
+        H[a][b] = s;
+      }
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+      double d = H[j][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d = fma(-H[j][k], H[j][k], d);
+      ok = ok && (d > 0.0);
+      const double l = sqrt(fmax(d, 1e-300));
+      const double il = 1.0 / l;
+      H[j][j] = l;
+#pragma unroll
+      for (int i = j + 1; i < NM; ++i) {
+        double s = H[i][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = fma(-H[i][k], H[j][k], s);
+        H[i][j] = s * il;
+      }
+    }
+    if (!ok) { *iters = it; return NEWTON_SINGULAR; }
+    double d[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      double s = G[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fma(-H[i][k], d[k], s);
+      d[i] = s / H[i][i];
+    }
+#pragma unroll
+    for (int i = NM - 1; i >= 0; --i) {
+      double s = d[i];
+#pragma unroll
+      for (int k = i + 1; k < NM; ++k) s = fma(-H[k][i], d[k], s);
+      d[i] = s / H[i][i];
+    }
+    double gd = 0.0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) gd = fma(G[k], d[k], gd);
+    // backtracking (Armijo) along lam + t d
+    double t = 1.0, Fc = 0.0;
+    bool accepted = false;
+    double lc[NM];
+    for (int ls = 0; ls < 40; ++ls) {
+#pragma unroll
+      for (int k = 0; k < NM; ++k) lc[k] = fma(t, d[k], lam[k]);
+      exp_family(lc, p);
+      Fc = dual_value(lc, p, m);
+      if (isfinite(Fc) && Fc <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = true; break; }
+      t *= 0.5;
+    }
+    ++it;
+    if (!accepted) { exp_family(lam, p); *iters = it; return NEWTON_MAXIT; }
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = lc[k];
+    F = Fc;
+  }
+}
+
+// exp(-(1 + lambda . P(xi_i))) for one velocity given at run time.
+__device__ __forceinline__ double exp_family_one(const double lam[NM], int cx, int cy) {
+  const double x = cx, y = cy, r2 = x * x + y * y;
+  double s = 1.0 + lam[0];
+  s = fma(lam[1], x, s);
+  s = fma(lam[2], y, s);
+  s = fma(lam[3], x * x, s);
+  s = fma(lam[4], x * y, s);
+  s = fma(lam[5], y * y, s);
+  s = fma(lam[6], x * r2, s);
+  s = fma(lam[7], y * r2, s);
+  return exp(-s);
+}
+
+// Grad's correction factors (Eqs. GradGeneral_f, GradGeneral_g) for one
+// velocity: cbar = c_i - u, sigma traceless viscous stress with mu = rho nu,
+// q = -kappa grad T with kappa = rho Cp nu (Pr = 1). du[a][b] = d_a u_b.
+__device__ __forceinline__ void grad_phi(const Params& pr, double rho, double T, double cbx,
+                                         double cby, const double du[2][2], const double dT[2],
+                                         double* phi_f, double* phi_g) {
+  const double mu = rho * pr.nu;
+  const double kappa = rho * pr.cp * pr.nu;
+  const double div = du[0][0] + du[1][1];
+  const double sxx = -mu * (2.0 * du[0][0] - div);
+  const double syy = -mu * (2.0 * du[1][1] - div);
+  const double sxy = -mu * (du[0][1] + du[1][0]);
+  const double qx = -kappa * dT[0];
+  const double qy = -kappa * dT[1];
+  const double c2 = cbx * cbx + cby * cby;
+  const double qc = qx * cbx + qy * cby;
+  const double iT = 1.0 / T;
+  *phi_f = (sxx * cbx * cbx + 2.0 * sxy * cbx * cby + syy * cby * cby) * (0.5 * iT * iT / rho) +
+           qc * (iT * iT / (rho * pr.cp)) * (0.5 * c2 * iT - pr.cp);
+  *phi_g = 2.0 * qc / (rho * pr.cp);
+}
+
+// Resolve a coordinate along one axis: periodic wrap or zero-gradient clamp.
+__device__ __forceinline__ int resolve(int x, int n, int bc, bool* ghost) {
+  if (bc == 0) {
+    int r = x % n;
+    if (r < 0) r += n;
+    return r;
+  }
+  if (x < 0) { *ghost = true; return 0; }
+  if (x >= n) { *ghost = true; return n - 1; }
+  return x;
+}
+
+// Warp-aggregated counter increment (all lanes of the warp must call it).
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, unsigned v) {
+  const unsigned s = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+
+}  // namespace alb

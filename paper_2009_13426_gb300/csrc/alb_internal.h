@@ -1,0 +1,50 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "alb_device.cuh"
+
+namespace alb {
+
+// Device counters, one slot each (64-bit).
+enum Counter {
+  CTR_NEWTON_ITERS = 0,
+  CTR_NEWTON_FAIL = 1,
+  CTR_REC = 2,
+  CTR_REC_FAIL = 3,
+  CTR_UNREALIZABLE = 4,
+  CTR_COUNT = 8
+};
+
+// Device state of one flow: double-buffered population, lattice and moment
+// planes. Plane p of buffer b starts at pop[b] + p * ps (elements).
+struct FlowDev {
+  Params prm;
+  int precision;     // 0 FP64 plain, 1 FP32 form
+  size_t n;          // nx * ny
+  size_t ps;         // plane stride in elements (n rounded up to 64)
+  void* pop[2];      // 42 planes of double or float
+  void* mom[2];      // 4 planes (rho, ux, uy, T) of double or float
+  uint8_t* lat[2];   // lattice code of the stored populations
+  uint8_t* nxt[2];   // lattice code selected for the next pull
+  unsigned long long* ctr;
+  int cur;           // buffer holding the current state
+};
+
+// Kernel launchers (alb_kernels.cu). All enqueue on `s` and return the launch error.
+cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, const double* rhouy,
+                        const double* rhoE, cudaStream_t s);
+cudaError_t launch_step(FlowDev& f, cudaStream_t s);
+cudaError_t launch_export_moments(const FlowDev& f, double* rho, double* rhoux, double* rhouy,
+                                  double* rhoE, cudaStream_t s);
+cudaError_t launch_export_shifts(const FlowDev& f, signed char* ux, signed char* uy,
+                                 cudaStream_t s);
+cudaError_t launch_equilibrium(const double* rho, const double* ubx, const double* uby,
+                               const double* T, int n, double tol, int maxit, double* feq,
+                               double* lambda, int* iters, int* status, cudaStream_t s);
+cudaError_t launch_select(const double* rho, const double* rhou, int n, double n0, int umax,
+                          signed char* out, cudaStream_t s);
+
+}  // namespace alb
