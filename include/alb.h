@@ -109,10 +109,13 @@ typedef struct {
 typedef struct {
   uint64_t steps;
   uint64_t node_updates;
-  uint64_t newton_iterations;       /* summed over node equilibria */
+  uint64_t newton_iterations;       /* FP64 Newton steps, node and rebuild equilibria */
   uint64_t newton_failures;         /* node equilibria that failed */
   uint64_t reconstructions;         /* missing pulls rebuilt (Grad) */
   uint64_t reconstruction_failures; /* rebuilds that fell back */
+  uint64_t newton_calls;            /* equilibrium solves, node and rebuild */
+  uint64_t fp64_evaluations;        /* FP64 evaluations of the 21 exponentials */
+  uint64_t fp32_iterations;         /* FP32 Newton steps (FP32 form) */
 } alb_stats;
 
 /* Fill *cfg with defaults: 64x64, D2Q21, u_max 2, nu 1e-3, gamma 1.4,

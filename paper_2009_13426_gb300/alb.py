@@ -58,7 +58,7 @@ class alb_config(ctypes.Structure):
 class alb_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "steps", "node_updates", "newton_iterations", "newton_failures", "reconstructions",
-        "reconstruction_failures")]
+        "reconstruction_failures", "newton_calls", "fp64_evaluations", "fp32_iterations")]
 
 
 _lib = None

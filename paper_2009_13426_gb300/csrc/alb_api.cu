@@ -323,6 +323,9 @@ int alb_stats_get(alb_handle* h, alb_stats* out) {
   out->newton_failures = h->ctr_host[CTR_NEWTON_FAIL];
   out->reconstructions = h->ctr_host[CTR_REC];
   out->reconstruction_failures = h->ctr_host[CTR_REC_FAIL];
+  out->newton_calls = h->ctr_host[CTR_NEWTON_CALLS];
+  out->fp64_evaluations = h->ctr_host[CTR_FP64_EVALS];
+  out->fp32_iterations = h->ctr_host[CTR_FP32_ITERS];
   return ALB_OK;
 }
 

@@ -150,14 +150,18 @@ __device__ __forceinline__ void maxwellian_guess(double ubx, double uby, double 
 // F(lambda) = sum_i p_i + lambda . m, whose gradient is -G/rho and Hessian the
 // exact Jacobian sum_i p_i P P^T. Stops at max_k |G_k|/rho <= tol. On return p
 // holds the equilibrium per unit density at lam.
-static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T, double tol, int maxit,
-                                        double lam[NM], double p[Q], int* iters) {
+// *iters counts Newton steps, *evals evaluations of the 21 exponentials.
+static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T, double tol,
+                                               int maxit, double lam[NM], double p[Q], int* iters,
+                                               int* evals) {
   *iters = 0;
+  *evals = 0;
   if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
   double m[NM];
   targets(ubx, uby, T, m);
   maxwellian_guess(ubx, uby, T, lam);
   exp_family(lam, p);
+  int ev = 2;
   double F = dual_value(lam, p, m);
   int it = 0;
   for (;;) {
@@ -172,9 +176,9 @@ static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T,
     double gmax = 0.0;
 #pragma unroll
     for (int k = 0; k < NM; ++k) gmax = fmax(gmax, fabs(G[k]));
-    if (!isfinite(gmax)) { *iters = it; return NEWTON_SINGULAR; }
-    if (gmax <= tol) { *iters = it; return NEWTON_OK; }
-    if (it >= maxit) { *iters = it; return NEWTON_MAXIT; }
+    if (!isfinite(gmax)) { *iters = it; *evals = ev; return NEWTON_SINGULAR; }
+    if (gmax <= tol) { *iters = it; *evals = ev; return NEWTON_OK; }
+    if (it >= maxit) { *iters = it; *evals = ev; return NEWTON_MAXIT; }
     // Jacobian (lower triangle), then in-place Cholesky factor
     double H[NM][NM];
 #pragma unroll
@@ -204,7 +208,7 @@ static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T,
         H[i][j] = s * il;
       }
     }
-    if (!ok) { *iters = it; return NEWTON_SINGULAR; }
+    if (!ok) { *iters = it; *evals = ev; return NEWTON_SINGULAR; }
     double d[NM];
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
@@ -231,12 +235,13 @@ static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T,
 #pragma unroll
       for (int k = 0; k < NM; ++k) lc[k] = fma(t, d[k], lam[k]);
       exp_family(lc, p);
+      ++ev;
       Fc = dual_value(lc, p, m);
       if (isfinite(Fc) && Fc <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = true; break; }
       t *= 0.5;
     }
     ++it;
-    if (!accepted) { exp_family(lam, p); *iters = it; return NEWTON_MAXIT; }
+    if (!accepted) { exp_family(lam, p); *iters = it; *evals = ev + 1; return NEWTON_MAXIT; }
 #pragma unroll
     for (int k = 0; k < NM; ++k) lam[k] = lc[k];
     F = Fc;

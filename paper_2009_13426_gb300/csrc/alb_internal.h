@@ -8,13 +8,17 @@
 
 namespace alb {
 
-// Device counters, one slot each (64-bit).
+// Device counters, one 64-bit slot each. Newton counts cover node and
+// rebuild equilibria; they feed the arithmetic roofline of the step.
 enum Counter {
-  CTR_NEWTON_ITERS = 0,
-  CTR_NEWTON_FAIL = 1,
-  CTR_REC = 2,
-  CTR_REC_FAIL = 3,
-  CTR_UNREALIZABLE = 4,
+  CTR_NEWTON_ITERS = 0,   // FP64 Newton steps (Jacobian + Cholesky + solve)
+  CTR_NEWTON_FAIL = 1,    // node equilibria that failed
+  CTR_REC = 2,            // rebuilt pulls
+  CTR_REC_FAIL = 3,       // rebuilds that fell back
+  CTR_UNREALIZABLE = 4,   // initial nodes with rho <= 0 or T <= 0
+  CTR_NEWTON_CALLS = 5,   // equilibrium solves (node + rebuild)
+  CTR_FP64_EVALS = 6,     // FP64 evaluations of the 21 exponentials
+  CTR_FP32_ITERS = 7,     // FP32 Newton steps
   CTR_COUNT = 8
 };
 

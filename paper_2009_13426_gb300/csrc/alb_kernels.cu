@@ -60,7 +60,8 @@ struct StepArgs {
 template <typename P>
 __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
                                          int cx, int cy, int Upx, int Upy, int sx, int sy,
-                                         double* fi, double* gi) {
+                                         double* fi, double* gi, unsigned* n_iters,
+                                         unsigned* n_evals) {
   bool gh = false;
   const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
   const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
@@ -86,9 +87,11 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
   const double ubx = ux - Upx, uby = uy - Upy;
   double lam[NM], p[Q];
-  int iters;
-  const int st = (rho > 0.0) ? newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &iters)
+  int iters = 0, evals = 0;
+  const int st = (rho > 0.0) ? newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &iters, &evals)
                              : NEWTON_UNREALIZABLE;
+  *n_iters += iters;
+  *n_evals += evals;
   const double gfac = (2.0 * pr.cv - 2.0) * T;
   if (st != NEWTON_OK) {
     if (T > 0.0) {
@@ -119,7 +122,7 @@ __device__ __forceinline__ void collide_store(const Params& pr, const P* st, int
                                               size_t ps, P* __restrict__ pop_out,
                                               P* __restrict__ mom_out, uint8_t* lat_out,
                                               uint8_t* nxt_out, unsigned* n_iters,
-                                              unsigned* n_fail) {
+                                              unsigned* n_evals, unsigned* n_fail) {
   const int Ux = lat_ux(code), Uy = lat_uy(code);
   Acc<P> ar, ajx, ajy, ae;
 #pragma unroll
@@ -142,10 +145,11 @@ __device__ __forceinline__ void collide_store(const Params& pr, const P* st, int
   const int code2 = lat_code(select_shift(ux, pr.n0, pr.umax), select_shift(uy, pr.n0, pr.umax));
 
   double lam[NM], p[Q];
-  int iters = 0;
-  const int ns = (rho > 0.0) ? newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &iters)
+  int iters = 0, evals = 0;
+  const int ns = (rho > 0.0) ? newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &iters, &evals)
                              : NEWTON_UNREALIZABLE;
   *n_iters += iters;
+  *n_evals += evals;
   if (ns == NEWTON_OK) {
     const double gfac = (2.0 * pr.cv - 2.0) * T;
     double tau = 0.5 + pr.nu / T;
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(StepArgs<P> a) {
   const Params& pr = a.prm;
   const int x = blockIdx.x * BLOCK + threadIdx.x;
   const int y = blockIdx.y;
-  unsigned n_rec = 0, n_rec_fail = 0, n_iters = 0, n_fail = 0;
+  unsigned n_rec = 0, n_rec_fail = 0, n_iters = 0, n_evals = 0, n_fail = 0, n_calls = 0;
   if (x < pr.nx) {
     const size_t k = (size_t)y * pr.nx + x;
     const size_t ps = a.ps;
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(StepArgs<P> a) {
         double fd, gd;
         n_rec += 1;
         n_rec_fail += rebuild_pull<P>(pr, a.mom_in, ps, XI_X(i), XI_Y(i), Upx, Upy, sx, sy, &fd,
-                                      &gd);
+                                      &gd, &n_iters, &n_evals);
         fi = (P)fd;
         gi = (P)gd;
       }
@@ -219,9 +223,12 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(StepArgs<P> a) {
       st[(Q + i) * BLOCK] = gi;
     }
     collide_store<P>(pr, st, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, &n_iters,
-                     &n_fail);
+                     &n_evals, &n_fail);
+    n_calls = 1 + n_rec;
   }
   warp_count(a.ctr + CTR_NEWTON_ITERS, n_iters);
+  warp_count(a.ctr + CTR_FP64_EVALS, n_evals);
+  warp_count(a.ctr + CTR_NEWTON_CALLS, n_calls);
   warp_count(a.ctr + CTR_NEWTON_FAIL, n_fail);
   warp_count(a.ctr + CTR_REC, n_rec);
   warp_count(a.ctr + CTR_REC_FAIL, n_rec_fail);
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
   const Params& pr = a.prm;
   const int x = blockIdx.x * BLOCK + threadIdx.x;
   const int y = blockIdx.y;
-  unsigned n_bad = 0, n_iters = 0, n_fail = 0;
+  unsigned n_bad = 0, n_iters = 0, n_evals = 0, n_fail = 0;
   if (x < pr.nx) {
     const size_t nx = (size_t)pr.nx;
     const size_t k = (size_t)y * nx + x;
@@ -281,10 +288,11 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
     const int U0x = select_shift(ux, pr.n0, pr.umax), U0y = select_shift(uy, pr.n0, pr.umax);
     const int code = lat_code(U0x, U0y);
     double lam[NM], p[Q];
-    int iters = 0;
+    int iters = 0, evals = 0;
     const bool realizable = (r > 0.0) && (T > 0.0) && isfinite(r) && isfinite(T);
-    const int ns = realizable ? newton_fp64(ux - U0x, uy - U0y, T, pr.tol, pr.maxit, lam, p, &iters)
-                              : NEWTON_UNREALIZABLE;
+    const int ns = realizable
+                       ? newton_fp64(ux - U0x, uy - U0y, T, pr.tol, pr.maxit, lam, p, &iters, &evals)
+                       : NEWTON_UNREALIZABLE;
     if (!realizable) n_bad += 1;
     if (ns != NEWTON_OK && realizable) n_fail += 1;
     const double gfac = (2.0 * pr.cv - 2.0) * T;
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
     }
     if (ns == NEWTON_OK) {
       collide_store<P>(pr, st, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out,
-                       &n_iters, &n_fail);
+                       &n_iters, &n_evals, &n_fail);
     } else {
       for (int i = 0; i < NPLANES; ++i) a.pop_out[i * a.ps + k] = (P)0;
       a.mom_out[k] = (P)r;
@@ -315,7 +323,6 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
     }
   }
   warp_count(a.ctr + CTR_UNREALIZABLE, n_bad);
-  warp_count(a.ctr + CTR_NEWTON_ITERS, n_iters);
   warp_count(a.ctr + CTR_NEWTON_FAIL, n_fail);
 }
 
@@ -349,9 +356,9 @@ __global__ void equilibrium_kernel(const double* rho, const double* ubx, const d
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   double lam[NM], p[Q];
-  int it = 0;
+  int it = 0, ev = 0;
   const double r = rho[k];
-  const int st = (r > 0.0) ? newton_fp64(ubx[k], uby[k], T[k], tol, maxit, lam, p, &it)
+  const int st = (r > 0.0) ? newton_fp64(ubx[k], uby[k], T[k], tol, maxit, lam, p, &it, &ev)
                            : NEWTON_UNREALIZABLE;
 #pragma unroll
   for (int i = 0; i < Q; ++i) feq[(size_t)k * Q + i] = r * p[i];
