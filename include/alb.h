@@ -151,6 +151,15 @@ int alb_moments(alb_handle* h, double* rho, double* rhoux, double* rhouy, double
 /* Lattice shift (U_x, U_y) of the current populations, one byte each per node. */
 int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where);
 
+/* Global totals of the current state: out[0..3] = sum over nodes of rho,
+ * rho ux, rho uy, rho E (host memory, 4 doubles). Mass, momentum and total
+ * energy are the invariants of the collision (Eqs. G0_8mom..G2yy_8mom with
+ * Eq. polyTemp); streaming preserves them except where pulls are rebuilt
+ * (Sec. III.B). Deterministic: a fixed chunking of the nodes and a fixed
+ * summation order, independent of the launch configuration. Synchronises the
+ * handle's stream. */
+int alb_totals(alb_handle* h, double* out);
+
 /* Counters (synchronises the handle's stream). */
 int alb_stats_get(alb_handle* h, alb_stats* out);
 

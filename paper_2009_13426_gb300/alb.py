@@ -73,6 +73,7 @@ _SIGS = {
     "alb_moments": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]),
     "alb_shifts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "alb_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(alb_stats)]),
+    "alb_totals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "alb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "alb_last_error": (ctypes.c_char_p, []),
     "alb_equilibrium": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_double,
@@ -197,6 +198,13 @@ def alb_destroy(h):
     return _check(lib().alb_destroy(h))
 
 
+def alb_totals(h):
+    """Sums of rho, rho*ux, rho*uy, rho*E over the grid (numpy array of 4)."""
+    out = np.zeros(4)
+    _check(lib().alb_totals(h, out.ctypes.data))
+    return out
+
+
 def alb_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lam=None, iters=None, status=None,
                     stream=None):
     """All arrays are torch CUDA tensors (float64; iters/status int32)."""
@@ -260,3 +268,6 @@ class Flow:
 
     def stats(self):
         return alb_stats_get(self.h)
+
+    def totals(self):
+        return alb_totals(self.h)

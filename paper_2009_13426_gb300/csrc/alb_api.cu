@@ -43,7 +43,10 @@ struct alb_handle {
   cudaStream_t stream;
   bool own_stream;
   double* staging;        // 4 * n doubles for host transfers
+  double* tot_partials;   // 4 doubles per chunk of the totals reduction
+  double* tot_out;        // 4 doubles, device result of the totals reduction
   unsigned long long* ctr_host;
+  double* tot_host;       // pinned copy of tot_out
   uint64_t steps;
   bool initialised;
 };
@@ -121,7 +124,10 @@ int alb_destroy(alb_handle* h) {
   }
   cudaFree(h->dev.ctr);
   cudaFree(h->staging);
+  cudaFree(h->tot_partials);
+  cudaFree(h->tot_out);
   cudaFreeHost(h->ctr_host);
+  cudaFreeHost(h->tot_host);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return ALB_OK;
@@ -196,8 +202,11 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   }
   ALLOC(d.ctr, CTR_COUNT * sizeof(unsigned long long));
   ALLOC(h->staging, 4 * d.n * sizeof(double));
+  ALLOC(h->tot_partials, (size_t)(totals_blocks((long long)d.n) + 1) * 4 * sizeof(double));
+  ALLOC(h->tot_out, 4 * sizeof(double));
 #undef ALLOC
-  if (cudaMallocHost((void**)&h->ctr_host, CTR_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&h->ctr_host, CTR_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->tot_host, 4 * sizeof(double)) != cudaSuccess) {
     alb_destroy(h);
     return fail(ALB_ENOMEM, "pinned host allocation failed");
   }
@@ -309,6 +318,17 @@ int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where) {
   ALB_CUDA(cudaMemcpyAsync(ux, s, n, cudaMemcpyDeviceToHost, h->stream), "alb_shifts: D2H");
   ALB_CUDA(cudaMemcpyAsync(uy, s + n, n, cudaMemcpyDeviceToHost, h->stream), "alb_shifts: D2H");
   ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_shifts: synchronise");
+  return ALB_OK;
+}
+
+int alb_totals(alb_handle* h, double* out) {
+  if (!h || !out) return fail(ALB_EINVAL, "alb_totals: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_totals: call alb_init first");
+  ALB_CUDA(launch_totals(h->dev, h->tot_partials, h->tot_out, h->stream), "alb_totals");
+  ALB_CUDA(cudaMemcpyAsync(h->tot_host, h->tot_out, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream), "alb_totals: D2H");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_totals: synchronise");
+  for (int j = 0; j < 4; ++j) out[j] = h->tot_host[j];
   return ALB_OK;
 }
 

@@ -37,6 +37,13 @@ struct FlowDev {
   int cur;           // buffer holding the current state
 };
 
+// Global totals (alb_totals.cu): one block per chunk of TOT_CHUNK nodes writes
+// 4 partial sums; a single block adds them in order.
+constexpr int TOT_THREADS = 256;
+constexpr long long TOT_CHUNK = 65536;
+int totals_blocks(long long n);
+cudaError_t launch_totals(const FlowDev& f, double* partials, double* out, cudaStream_t s);
+
 // Kernel launchers (alb_kernels.cu). All enqueue on `s` and return the launch error.
 cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, const double* rhouy,
                         const double* rhoE, cudaStream_t s);

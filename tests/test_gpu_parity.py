@@ -220,3 +220,35 @@ def test_device_pointer_init_and_moments(alb):
     torch.cuda.synchronize()
     for a, b in zip(out, host.moments()):
         assert np.array_equal(a.cpu().numpy().reshape(32, 32), b)
+
+
+# --------------------------------------------------------------- global totals
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_totals_match_host_sums(alb, precision):
+    """alb_totals equals the sums of the exported fields; two chunks plus a
+    ragged tail (300 x 300 = 90000 nodes, chunks of 65536)."""
+    fields = flows.isentropic_vortex(300, 300, radius=20.0, mach=0.8)
+    fl = run_gpu(alb, 300, 300, fields, 5, precision)
+    tot = fl.totals()
+    ref = np.array([m.sum() for m in fl.moments()])
+    np.testing.assert_allclose(tot, ref, rtol=1e-12)
+    assert np.array_equal(tot, fl.totals())  # deterministic
+
+
+def test_totals_conserved_without_lattice_changes(alb):
+    """Collision and plain streaming conserve mass, momentum and energy: with
+    no lattice change (no rebuild) the totals drift only by the Newton
+    tolerance per node and step."""
+    n = 96
+    fields = flows.isentropic_vortex(n, n, strength=1.0, radius=8.0, mach=0.0, noise=0.0)
+    fl = alb.Flow(n, n, nu=1e-2)
+    fl.init(*fields)
+    t0 = fl.totals()
+    fl.step(30)
+    fl.sync()
+    assert fl.stats()["reconstructions"] == 0
+    t1 = fl.totals()
+    assert abs(t1[0] - t0[0]) <= 30 * 1e-12 * t0[0]
+    assert abs(t1[3] - t0[3]) <= 30 * 1e-12 * t0[3]
+    assert abs(t1[1] - t0[1]) <= 30 * 1e-12 * t0[0]
