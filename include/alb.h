@@ -160,6 +160,28 @@ int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where);
  * handle's stream. */
 int alb_totals(alb_handle* h, double* out);
 
+/* Global totals without any allocation, for callers that cannot allocate
+ * device memory (for example code that runs while another component owns
+ * every allocation, or a context where cudaMalloc is not allowed). The paper
+ * has no counterpart: this is a service of the library, not a step of the
+ * method.
+ *   rho, rhoux, rhouy, rhoE: device arrays of n doubles each (conserved
+ *       fields, e.g. from alb_moments(..., ALB_DEVICE)), read only.
+ *   n:   number of nodes, 0 <= n <= 268,435,456 (4096 chunks of 65536);
+ *        larger n returns ALB_EINVAL and launches nothing.
+ *   out: device array of 4 doubles, receives the sums of the four fields.
+ *   stream: cudaStream_t (NULL: the legacy default stream); asynchronous.
+ * The partial sums live in a 128 KB static device array that every GPU that
+ * loads the library holds until the process exits; nothing is allocated or
+ * freed. The first call on a device looks up the array's device address with
+ * that device current: make that first call before any stream capture.
+ * Calls share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong sums; serialise them. Each call writes every
+ * partial it reads, so no state carries over between calls. Same chunking
+ * and summation order as alb_totals. */
+int alb_totals_noalloc(const double* rho, const double* rhoux, const double* rhouy,
+                       const double* rhoE, long long n, double* out, void* stream);
+
 /* Counters (synchronises the handle's stream). */
 int alb_stats_get(alb_handle* h, alb_stats* out);
 

@@ -74,6 +74,8 @@ _SIGS = {
     "alb_shifts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "alb_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(alb_stats)]),
     "alb_totals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "alb_totals_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_longlong,
+                                                                  ctypes.c_void_p, ctypes.c_void_p]),
     "alb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "alb_last_error": (ctypes.c_char_p, []),
     "alb_equilibrium": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_double,
@@ -203,6 +205,13 @@ def alb_totals(h):
     out = np.zeros(4)
     _check(lib().alb_totals(h, out.ctypes.data))
     return out
+
+
+def alb_totals_noalloc(rho, rhoux, rhouy, rhoE, n, out, stream=None):
+    """Totals of four device fields into the device array `out` (4 doubles)
+    without allocating: for callers that cannot allocate device memory."""
+    return _check(lib().alb_totals_noalloc(_ptr(rho), _ptr(rhoux), _ptr(rhouy), _ptr(rhoE),
+                                           int(n), _ptr(out), _stream(stream)))
 
 
 def alb_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lam=None, iters=None, status=None,

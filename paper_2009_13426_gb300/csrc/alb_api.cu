@@ -332,6 +332,24 @@ int alb_totals(alb_handle* h, double* out) {
   return ALB_OK;
 }
 
+// For callers that cannot allocate device memory: the totals of caller-owned
+// conserved fields, with the partial sums in a static device array. The first
+// call on a device looks the array's address up (with that device current);
+// make that first call before any stream capture. Calls that overlap on the
+// GPU share the array and race.
+int alb_totals_noalloc(const double* rho, const double* rhoux, const double* rhouy,
+                       const double* rhoE, long long n, double* out, void* stream) {
+  if (n < 0 || !out || (n > 0 && (!rho || !rhoux || !rhouy || !rhoE)))
+    return fail(ALB_EINVAL, "alb_totals_noalloc: bad arguments");
+  if (n > noalloc_max_nodes())
+    return fail(ALB_EINVAL,
+                "alb_totals_noalloc: n = %lld exceeds the %lld nodes its static scratch holds",
+                n, noalloc_max_nodes());
+  ALB_CUDA(launch_totals_noalloc(rho, rhoux, rhouy, rhoE, n, out, (cudaStream_t)stream),
+           "alb_totals_noalloc");
+  return ALB_OK;
+}
+
 int alb_stats_get(alb_handle* h, alb_stats* out) {
   if (!h || !out) return fail(ALB_EINVAL, "alb_stats_get: null pointer");
   ALB_CUDA(cudaMemcpyAsync(h->ctr_host, h->dev.ctr, CTR_COUNT * sizeof(unsigned long long),

@@ -43,6 +43,11 @@ constexpr int TOT_THREADS = 256;
 constexpr long long TOT_CHUNK = 65536;
 int totals_blocks(long long n);
 cudaError_t launch_totals(const FlowDev& f, double* partials, double* out, cudaStream_t s);
+// Same reduction over caller-owned conserved fields, with its partial sums in
+// a file-scope device array (no allocation); n <= noalloc_max_nodes().
+long long noalloc_max_nodes();
+cudaError_t launch_totals_noalloc(const double* rho, const double* rhoux, const double* rhouy,
+                                  const double* rhoE, long long n, double* out, cudaStream_t s);
 
 // Kernel launchers (alb_kernels.cu). All enqueue on `s` and return the launch error.
 cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, const double* rhouy,

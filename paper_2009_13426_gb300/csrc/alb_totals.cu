@@ -4,6 +4,8 @@
 // TOT_CHUNK nodes, one block per chunk; every block writes its four partial
 // sums to a scratch array, and one block then adds the partials in index
 // order. The result depends only on n, never on the launch configuration.
+#include <mutex>
+
 #include "alb_internal.h"
 
 namespace alb {
@@ -21,6 +23,17 @@ struct MomentPlanes {
     v[1] = r * ux;
     v[2] = r * uy;
     v[3] = 0.5 * r * (ux * ux + uy * uy) + r * cv * T;
+  }
+};
+
+// Four conserved fields given by the caller as separate double arrays.
+struct ConservedFields {
+  const double *rho, *rhoux, *rhouy, *rhoE;
+  __device__ __forceinline__ void get(size_t k, double v[4]) const {
+    v[0] = rho[k];
+    v[1] = rhoux[k];
+    v[2] = rhouy[k];
+    v[3] = rhoE[k];
   }
 };
 
@@ -85,6 +98,53 @@ cudaError_t launch_totals(const FlowDev& f, double* partials, double* out, cudaS
                              (long long)f.n, partials, out, s);
   return launch_totals_src(MomentPlanes<float>{(const float*)f.mom[f.cur], f.ps, f.prm.cv},
                            (long long)f.n, partials, out, s);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free totals for callers that cannot allocate device memory.
+//
+// The partial sums live in a file-scope device array instead of memory from
+// cudaMalloc. Every GPU that loads this library holds the array until the
+// process exits. In host code the array's name is only a host-side stand-in
+// for the symbol, so its device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+
+constexpr int NOALLOC_MAX_CHUNKS = 4096;  // up to 4096 * 65536 = 268,435,456 nodes
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_CHUNKS * 4];
+
+static double* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+long long noalloc_max_nodes() { return (long long)NOALLOC_MAX_CHUNKS * TOT_CHUNK; }
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device).
+static cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_totals_noalloc(const double* rho, const double* rhoux, const double* rhouy,
+                                  const double* rhoE, long long n, double* out, cudaStream_t s) {
+  double* partials = nullptr;
+  cudaError_t e = noalloc_scratch(&partials);
+  if (e != cudaSuccess) return e;
+  // Every partial the final pass reads is written by the partial pass of the
+  // same call, so nothing left by an earlier call is ever read.
+  return launch_totals_src(ConservedFields{rho, rhoux, rhouy, rhoE}, n, partials, out, s);
 }
 
 }  // namespace alb
