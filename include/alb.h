@@ -195,15 +195,25 @@ const char* alb_last_error(void);
  * Stateless device entry points (device pointers, current device, stream
  * may be NULL for the legacy default stream). */
 
-/* Numerical equilibrium (Eqs. exponential, feqNum_8Mom; FP64 Newton) of n
- * states given in the lattice frame: rho[k], relative velocity (ubx[k], uby[k])
- * and T[k]. Writes feq[k*21 + i] (velocity order of alb_velocities),
- * lambda[k*8 + j] if lambda != NULL (order 0, x, y, xx, xy, yy, x|xi|^2,
- * y|xi|^2), iters[k] and status[k] (0 converged, 1 not converged,
- * 2 singular / non-finite, 3 unrealizable input) if non-NULL. */
+/* Numerical equilibrium (Eqs. exponential, feqNum_8Mom, constraints
+ * G0_8mom..G3yaa_8mom) of n states given in the lattice frame: rho[k],
+ * relative velocity (ubx[k], uby[k]) and T[k]; stop at max|G|/rho <= tol.
+ * precision selects the solver of the step kernels: ALB_FP64_PLAIN, damped
+ * Newton in FP64; ALB_FP32_FORM, Newton in FP32 refined with FP64 residuals
+ * (full FP64 Newton if that fails). Writes feq[k*21 + i] (velocity order of
+ * alb_velocities), lambda[k*8 + j] if lambda != NULL (order 0, x, y, xx, xy,
+ * yy, x|xi|^2, y|xi|^2), iters[k] (FP64 Newton steps, or FP64 residual
+ * evaluations for ALB_FP32_FORM) and status[k] (0 converged, 1 not
+ * converged, 2 singular / non-finite, 3 unrealizable input) if non-NULL. */
 int alb_equilibrium(const double* rho, const double* ubx, const double* uby, const double* T,
-                    int n, double tol, int maxit, double* feq, double* lambda, int* iters,
-                    int* status, void* stream);
+                    int n, double tol, int maxit, int precision, double* feq, double* lambda,
+                    int* iters, int* status, void* stream);
+
+/* out[k] = exp(-s[k]) by the table-driven FP64 exponential that the FP32
+ * form's equilibrium uses (Tang's method: 32-entry table of 2^(j/32), degree-6
+ * polynomial on |r| <= ln2/64). 0 below 2^-1022, +inf from 2^1024 on. Device
+ * arrays of n doubles. Exposed so that its accuracy can be checked. */
+int alb_exp_neg(const double* s, int n, double* out, void* stream);
 
 /* Shift criterion (Eq. criterion with offset n0, clamped to +-u_max) applied
  * to u[k] = rhou[k] / rho[k] in FP64 for n values; writes out[k]. */

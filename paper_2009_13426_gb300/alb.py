@@ -79,7 +79,10 @@ _SIGS = {
     "alb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "alb_last_error": (ctypes.c_char_p, []),
     "alb_equilibrium": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_double,
-                                                                ctypes.c_int] + [ctypes.c_void_p] * 5),
+                                                                ctypes.c_int, ctypes.c_int]
+                        + [ctypes.c_void_p] * 5),
+    "alb_exp_neg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
     "alb_select_shift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -215,11 +218,16 @@ def alb_totals_noalloc(rho, rhoux, rhouy, rhoE, n, out, stream=None):
 
 
 def alb_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lam=None, iters=None, status=None,
-                    stream=None):
+                    stream=None, precision=ALB_FP64_PLAIN):
     """All arrays are torch CUDA tensors (float64; iters/status int32)."""
     return _check(lib().alb_equilibrium(_ptr(rho), _ptr(ubx), _ptr(uby), _ptr(T), int(n),
-                                        float(tol), int(maxit), _ptr(feq), _ptr(lam), _ptr(iters),
-                                        _ptr(status), _stream(stream)))
+                                        float(tol), int(maxit), int(precision), _ptr(feq),
+                                        _ptr(lam), _ptr(iters), _ptr(status), _stream(stream)))
+
+
+def alb_exp_neg(s, n, out, stream=None):
+    """out = exp(-s) by the library's table-driven FP64 exponential (CUDA tensors)."""
+    return _check(lib().alb_exp_neg(_ptr(s), int(n), _ptr(out), _stream(stream)))
 
 
 def alb_select_shift(rho, rhou, n, n0, u_max, out, stream=None):

@@ -121,6 +121,7 @@ int alb_destroy(alb_handle* h) {
     cudaFree(h->dev.mom[b]);
     cudaFree(h->dev.lat[b]);
     cudaFree(h->dev.nxt[b]);
+    cudaFree(h->dev.lam[b]);
   }
   cudaFree(h->dev.ctr);
   cudaFree(h->staging);
@@ -199,6 +200,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
     ALLOC(d.mom[b], 4 * d.ps * es);
     ALLOC(d.lat[b], d.ps);
     ALLOC(d.nxt[b], d.ps);
+    if (d.precision == ALB_FP32_FORM) ALLOC(d.lam[b], NM * d.ps * sizeof(float));
   }
   ALLOC(d.ctr, CTR_COUNT * sizeof(unsigned long long));
   ALLOC(h->staging, 4 * d.n * sizeof(double));
@@ -368,13 +370,21 @@ int alb_stats_get(alb_handle* h, alb_stats* out) {
 }
 
 int alb_equilibrium(const double* rho, const double* ubx, const double* uby, const double* T,
-                    int n, double tol, int maxit, double* feq, double* lambda, int* iters,
-                    int* status, void* stream) {
+                    int n, double tol, int maxit, int precision, double* feq, double* lambda,
+                    int* iters, int* status, void* stream) {
   if (n < 0 || (n > 0 && (!rho || !ubx || !uby || !T || !feq)))
     return fail(ALB_EINVAL, "alb_equilibrium: bad arguments");
   if (!(tol > 0.0) || maxit < 1) return fail(ALB_EINVAL, "alb_equilibrium: bad tolerance");
-  ALB_CUDA(launch_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lambda, iters, status,
-                              (cudaStream_t)stream), "alb_equilibrium");
+  if (precision != ALB_FP64_PLAIN && precision != ALB_FP32_FORM)
+    return fail(ALB_EINVAL, "alb_equilibrium: unknown precision %d", precision);
+  ALB_CUDA(launch_equilibrium(rho, ubx, uby, T, n, tol, maxit, precision, feq, lambda, iters,
+                              status, (cudaStream_t)stream), "alb_equilibrium");
+  return ALB_OK;
+}
+
+int alb_exp_neg(const double* s, int n, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!s || !out))) return fail(ALB_EINVAL, "alb_exp_neg: bad arguments");
+  ALB_CUDA(launch_exp_neg(s, n, out, (cudaStream_t)stream), "alb_exp_neg");
   return ALB_OK;
 }
 

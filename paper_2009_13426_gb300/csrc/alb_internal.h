@@ -33,6 +33,7 @@ struct FlowDev {
   void* mom[2];      // 4 planes (rho, ux, uy, T) of double or float
   uint8_t* lat[2];   // lattice code of the stored populations
   uint8_t* nxt[2];   // lattice code selected for the next pull
+  float* lam[2];     // FP32 form: 8 planes of multipliers (warm start); else null
   unsigned long long* ctr;
   int cur;           // buffer holding the current state
 };
@@ -58,8 +59,10 @@ cudaError_t launch_export_moments(const FlowDev& f, double* rho, double* rhoux, 
 cudaError_t launch_export_shifts(const FlowDev& f, signed char* ux, signed char* uy,
                                  cudaStream_t s);
 cudaError_t launch_equilibrium(const double* rho, const double* ubx, const double* uby,
-                               const double* T, int n, double tol, int maxit, double* feq,
-                               double* lambda, int* iters, int* status, cudaStream_t s);
+                               const double* T, int n, double tol, int maxit, int precision,
+                               double* feq, double* lambda, int* iters, int* status,
+                               cudaStream_t s);
+cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s);
 cudaError_t launch_select(const double* rho, const double* rhou, int n, double n0, int umax,
                           signed char* out, cudaStream_t s);
 

@@ -10,11 +10,50 @@
 //
 // Layout: structure of arrays. Plane p (f_0..f_20, g_0..g_20) of a buffer is
 // a contiguous nx*ny array, x fastest; lattice codes and moments likewise.
+#include <type_traits>
+
 #include "alb_internal.h"
+#include "alb_mixed.cuh"
 
 namespace alb {
 
 constexpr int BLOCK = 128;
+
+// Equilibrium of one node in the storage precision P: the full FP64 Newton for
+// the FP64 plain path, the mixed FP32/FP64 solver for the FP32 form.
+template <typename P>
+__device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, double uby,
+                                                double T, const double* tab, const float* warm,
+                                                double lam[NM], double p[Q], SolveCount* cnt) {
+  if constexpr (std::is_same<P, float>::value) {
+    return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, lam, p, cnt);
+  } else {
+    int it = 0, ev = 0;
+    const int st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev);
+    cnt->fp64_iters += it;
+    cnt->fp64_evals += ev;
+    return st;
+  }
+}
+
+// exp(-(1 + lambda . P(xi))) for one velocity (cx, cy) given at run time.
+template <typename P>
+__device__ __forceinline__ double p_one(const double lam[NM], int cx, int cy, const double* tab) {
+  if constexpr (std::is_same<P, float>::value) {
+    const double x = cx, y = cy, r2 = x * x + y * y;
+    double s = 1.0 + lam[0];
+    s = fma(lam[1], x, s);
+    s = fma(lam[2], y, s);
+    s = fma(lam[3], x * x, s);
+    s = fma(lam[4], x * y, s);
+    s = fma(lam[5], y * y, s);
+    s = fma(lam[6], x * r2, s);
+    s = fma(lam[7], y * r2, s);
+    return exp_neg(s, tab);
+  } else {
+    return exp_family_one(lam, cx, cy);
+  }
+}
 
 // Moment accumulation: plain in FP64; Neumaier-compensated in FP32.
 template <typename P>
@@ -47,10 +86,28 @@ struct StepArgs {
   const uint8_t* nxt_in;
   uint8_t* lat_out;
   uint8_t* nxt_out;
+  const float* lam_in;  // FP32 form: multipliers of the previous step (8 planes)
+  float* lam_out;
   size_t ps;
   Params prm;
   unsigned long long* ctr;
 };
+
+// Multipliers stored for node k (8 planes), moved into the frame of lattice
+// (Ux, Uy) from the lattice code they were computed in.
+__device__ __forceinline__ void load_warm(const float* lam, size_t ps, size_t k, int code_from,
+                                          int Ux, int Uy, float w[NM]) {
+  float l[NM];
+#pragma unroll
+  for (int j = 0; j < NM; ++j) l[j] = lam[j * ps + k];
+  const int dx = lat_ux(code_from) - Ux, dy = lat_uy(code_from) - Uy;
+  if (dx == 0 && dy == 0) {
+#pragma unroll
+    for (int j = 0; j < NM; ++j) w[j] = l[j];
+  } else {
+    shift_multipliers(l, (float)dx, (float)dy, w);
+  }
+}
 
 // Grad rebuild of a missing pull (Sec. III.B.2, IV.A.3): the post-collision
 // population of velocity (cx, cy) in the receiver's lattice (Upx, Upy), built
@@ -60,8 +117,9 @@ struct StepArgs {
 template <typename P>
 __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
                                          int cx, int cy, int Upx, int Upy, int sx, int sy,
-                                         double* fi, double* gi, unsigned* n_iters,
-                                         unsigned* n_evals) {
+                                         double* fi, double* gi, const double* tab,
+                                         const float* lam_in, const uint8_t* lat_in,
+                                         SolveCount* cnt) {
   bool gh = false;
   const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
   const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
@@ -87,11 +145,14 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
   const double ubx = ux - Upx, uby = uy - Upy;
   double lam[NM], p[Q];
-  int iters = 0, evals = 0;
-  const int st = (rho > 0.0) ? newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &iters, &evals)
+  float wbuf[NM];
+  const float* warm = nullptr;
+  if constexpr (std::is_same<P, float>::value) {
+    load_warm(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
+    warm = wbuf;
+  }
+  const int st = (rho > 0.0) ? node_equilibrium<P>(pr, ubx, uby, T, tab, warm, lam, p, cnt)
                              : NEWTON_UNREALIZABLE;
-  *n_iters += iters;
-  *n_evals += evals;
   const double gfac = (2.0 * pr.cv - 2.0) * T;
   if (st != NEWTON_OK) {
     if (T > 0.0) {
@@ -105,7 +166,7 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   }
   const double tau = 0.5 + pr.nu / T;
   const double omega = 1.0 - 1.0 / tau;
-  const double feq = rho * exp_family_one(lam, cx, cy);
+  const double feq = rho * p_one<P>(lam, cx, cy, tab);
   const double cbx = (double)(cx + Upx) - ux;
   const double cby = (double)(cy + Upy) - uy;
   double phf, phg;
@@ -121,8 +182,9 @@ template <typename P>
 __device__ __forceinline__ void collide_store(const Params& pr, const P* st, int code, size_t k,
                                               size_t ps, P* __restrict__ pop_out,
                                               P* __restrict__ mom_out, uint8_t* lat_out,
-                                              uint8_t* nxt_out, unsigned* n_iters,
-                                              unsigned* n_evals, unsigned* n_fail) {
+                                              uint8_t* nxt_out, const double* tab,
+                                              const float* warm, float* lam_out,
+                                              SolveCount* cnt, unsigned* n_fail) {
   const int Ux = lat_ux(code), Uy = lat_uy(code);
   Acc<P> ar, ajx, ajy, ae;
 #pragma unroll
@@ -145,11 +207,21 @@ __device__ __forceinline__ void collide_store(const Params& pr, const P* st, int
   const int code2 = lat_code(select_shift(ux, pr.n0, pr.umax), select_shift(uy, pr.n0, pr.umax));
 
   double lam[NM], p[Q];
-  int iters = 0, evals = 0;
-  const int ns = (rho > 0.0) ? newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &iters, &evals)
+  const int ns = (rho > 0.0) ? node_equilibrium<P>(pr, ubx, uby, T, tab, warm, lam, p, cnt)
                              : NEWTON_UNREALIZABLE;
-  *n_iters += iters;
-  *n_evals += evals;
+  if constexpr (std::is_same<P, float>::value) {
+    // multipliers for the next step's warm start (lattice `code`)
+    if (ns == NEWTON_OK) {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = (float)lam[j];
+    } else if (warm) {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = warm[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = j == 3 || j == 5 ? 0.5f : 0.0f;
+    }
+  }
   if (ns == NEWTON_OK) {
     const double gfac = (2.0 * pr.cv - 2.0) * T;
     double tau = 0.5 + pr.nu / T;
@@ -187,13 +259,17 @@ __device__ __forceinline__ void collide_store(const Params& pr, const P* st, int
 }
 
 template <typename P>
-__global__ void __launch_bounds__(BLOCK) step_kernel(StepArgs<P> a) {
+__global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1))
+    step_kernel(StepArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_tab[32];
+  load_exptab(s_tab);
   P* st = reinterpret_cast<P*>(smem_raw) + threadIdx.x;
   const Params& pr = a.prm;
   const int x = blockIdx.x * BLOCK + threadIdx.x;
   const int y = blockIdx.y;
-  unsigned n_rec = 0, n_rec_fail = 0, n_iters = 0, n_evals = 0, n_fail = 0, n_calls = 0;
+  unsigned n_rec = 0, n_rec_fail = 0, n_fail = 0, n_calls = 0;
+  SolveCount cnt;
   if (x < pr.nx) {
     const size_t k = (size_t)y * pr.nx + x;
     const size_t ps = a.ps;
@@ -215,19 +291,26 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(StepArgs<P> a) {
         double fd, gd;
         n_rec += 1;
         n_rec_fail += rebuild_pull<P>(pr, a.mom_in, ps, XI_X(i), XI_Y(i), Upx, Upy, sx, sy, &fd,
-                                      &gd, &n_iters, &n_evals);
+                                      &gd, s_tab, a.lam_in, a.lat_in, &cnt);
         fi = (P)fd;
         gi = (P)gd;
       }
       st[i * BLOCK] = fi;
       st[(Q + i) * BLOCK] = gi;
     }
-    collide_store<P>(pr, st, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, &n_iters,
-                     &n_evals, &n_fail);
+    float wbuf[NM];
+    const float* warm = nullptr;
+    if constexpr (std::is_same<P, float>::value) {
+      load_warm(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
+      warm = wbuf;
+    }
+    collide_store<P>(pr, st, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,
+                     warm, a.lam_out, &cnt, &n_fail);
     n_calls = 1 + n_rec;
   }
-  warp_count(a.ctr + CTR_NEWTON_ITERS, n_iters);
-  warp_count(a.ctr + CTR_FP64_EVALS, n_evals);
+  warp_count(a.ctr + CTR_NEWTON_ITERS, cnt.fp64_iters);
+  warp_count(a.ctr + CTR_FP64_EVALS, cnt.fp64_evals);
+  warp_count(a.ctr + CTR_FP32_ITERS, cnt.fp32_iters);
   warp_count(a.ctr + CTR_NEWTON_CALLS, n_calls);
   warp_count(a.ctr + CTR_NEWTON_FAIL, n_fail);
   warp_count(a.ctr + CTR_REC, n_rec);
@@ -241,6 +324,7 @@ struct InitArgs {
   P* mom_out;
   uint8_t* lat_out;
   uint8_t* nxt_out;
+  float* lam_out;
   size_t ps;
   Params prm;
   unsigned long long* ctr;
@@ -261,11 +345,14 @@ __device__ __forceinline__ void init_prim(const double* rho, const double* rhoux
 template <typename P>
 __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_tab[32];
+  load_exptab(s_tab);
   P* st = reinterpret_cast<P*>(smem_raw) + threadIdx.x;
   const Params& pr = a.prm;
   const int x = blockIdx.x * BLOCK + threadIdx.x;
   const int y = blockIdx.y;
-  unsigned n_bad = 0, n_iters = 0, n_evals = 0, n_fail = 0;
+  unsigned n_bad = 0, n_fail = 0;
+  SolveCount cnt;
   if (x < pr.nx) {
     const size_t nx = (size_t)pr.nx;
     const size_t k = (size_t)y * nx + x;
@@ -288,10 +375,9 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
     const int U0x = select_shift(ux, pr.n0, pr.umax), U0y = select_shift(uy, pr.n0, pr.umax);
     const int code = lat_code(U0x, U0y);
     double lam[NM], p[Q];
-    int iters = 0, evals = 0;
     const bool realizable = (r > 0.0) && (T > 0.0) && isfinite(r) && isfinite(T);
     const int ns = realizable
-                       ? newton_fp64(ux - U0x, uy - U0y, T, pr.tol, pr.maxit, lam, p, &iters, &evals)
+                       ? node_equilibrium<P>(pr, ux - U0x, uy - U0y, T, s_tab, nullptr, lam, p, &cnt)
                        : NEWTON_UNREALIZABLE;
     if (!realizable) n_bad += 1;
     if (ns != NEWTON_OK && realizable) n_fail += 1;
@@ -310,8 +396,15 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
       st[(Q + i) * BLOCK] = (P)(gfac * feq * (1.0 + phg));
     }
     if (ns == NEWTON_OK) {
+      float wbuf[NM];
+      const float* warm = nullptr;
+      if constexpr (std::is_same<P, float>::value) {
+#pragma unroll
+        for (int j = 0; j < NM; ++j) wbuf[j] = (float)lam[j];
+        warm = wbuf;
+      }
       collide_store<P>(pr, st, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out,
-                       &n_iters, &n_evals, &n_fail);
+                       s_tab, warm, a.lam_out, &cnt, &n_fail);
     } else {
       for (int i = 0; i < NPLANES; ++i) a.pop_out[i * a.ps + k] = (P)0;
       a.mom_out[k] = (P)r;
@@ -320,6 +413,9 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
       a.mom_out[3 * a.ps + k] = (P)T;
       a.lat_out[k] = (uint8_t)code;
       a.nxt_out[k] = (uint8_t)code;
+      if constexpr (std::is_same<P, float>::value)
+#pragma unroll
+        for (int j = 0; j < NM; ++j) a.lam_out[j * a.ps + k] = j == 3 || j == 5 ? 0.5f : 0.0f;
     }
   }
   warp_count(a.ctr + CTR_UNREALIZABLE, n_bad);
@@ -351,22 +447,37 @@ __global__ void export_shifts_kernel(const uint8_t* lat, size_t n, signed char* 
 }
 
 __global__ void equilibrium_kernel(const double* rho, const double* ubx, const double* uby,
-                                   const double* T, int n, double tol, int maxit, double* feq,
-                                   double* lambda, int* iters, int* status) {
+                                   const double* T, int n, double tol, int maxit, int precision,
+                                   double* feq, double* lambda, int* iters, int* status) {
+  __shared__ double s_tab[32];
+  load_exptab(s_tab);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   double lam[NM], p[Q];
-  int it = 0, ev = 0;
   const double r = rho[k];
-  const int st = (r > 0.0) ? newton_fp64(ubx[k], uby[k], T[k], tol, maxit, lam, p, &it, &ev)
-                           : NEWTON_UNREALIZABLE;
+  Params pr{};
+  pr.tol = tol;
+  pr.maxit = maxit;
+  SolveCount cnt;
+  int st = NEWTON_UNREALIZABLE;
+  if (r > 0.0)
+    st = precision == 0
+             ? node_equilibrium<double>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, lam, p, &cnt)
+             : node_equilibrium<float>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, lam, p, &cnt);
 #pragma unroll
   for (int i = 0; i < Q; ++i) feq[(size_t)k * Q + i] = r * p[i];
   if (lambda)
 #pragma unroll
     for (int j = 0; j < NM; ++j) lambda[(size_t)k * NM + j] = lam[j];
-  if (iters) iters[k] = it;
+  if (iters) iters[k] = precision == 0 ? (int)cnt.fp64_iters : (int)cnt.fp64_evals;
   if (status) status[k] = st;
+}
+
+__global__ void exp_neg_kernel(const double* s, int n, double* out) {
+  __shared__ double s_tab[32];
+  load_exptab(s_tab);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = exp_neg(s[k], s_tab);
 }
 
 __global__ void select_kernel(const double* rho, const double* rhou, int n, double n0, int umax,
@@ -385,11 +496,11 @@ cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, cons
   const int out = f.cur;
   if (f.precision == 0) {
     InitArgs<double> a{rho, rhoux, rhouy, rhoE, (double*)f.pop[out], (double*)f.mom[out],
-                       f.lat[out], f.nxt[out], f.ps, f.prm, f.ctr};
+                       f.lat[out], f.nxt[out], nullptr, f.ps, f.prm, f.ctr};
     init_kernel<double><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(double), s>>>(a);
   } else {
     InitArgs<float> a{rho, rhoux, rhouy, rhoE, (float*)f.pop[out], (float*)f.mom[out],
-                      f.lat[out], f.nxt[out], f.ps, f.prm, f.ctr};
+                      f.lat[out], f.nxt[out], f.lam[out], f.ps, f.prm, f.ctr};
     init_kernel<float><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(float), s>>>(a);
   }
   return cudaGetLastError();
@@ -400,12 +511,12 @@ cudaError_t launch_step(FlowDev& f, cudaStream_t s) {
   if (f.precision == 0) {
     StepArgs<double> a{(const double*)f.pop[in], (double*)f.pop[out], (const double*)f.mom[in],
                        (double*)f.mom[out], f.lat[in], f.nxt[in], f.lat[out], f.nxt[out],
-                       f.ps, f.prm, f.ctr};
+                       nullptr, nullptr, f.ps, f.prm, f.ctr};
     step_kernel<double><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(double), s>>>(a);
   } else {
     StepArgs<float> a{(const float*)f.pop[in], (float*)f.pop[out], (const float*)f.mom[in],
                       (float*)f.mom[out], f.lat[in], f.nxt[in], f.lat[out], f.nxt[out],
-                      f.ps, f.prm, f.ctr};
+                      f.lam[in], f.lam[out], f.ps, f.prm, f.ctr};
     step_kernel<float><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(float), s>>>(a);
   }
   cudaError_t e = cudaGetLastError();
@@ -433,11 +544,18 @@ cudaError_t launch_export_shifts(const FlowDev& f, signed char* ux, signed char*
 }
 
 cudaError_t launch_equilibrium(const double* rho, const double* ubx, const double* uby,
-                               const double* T, int n, double tol, int maxit, double* feq,
-                               double* lambda, int* iters, int* status, cudaStream_t s) {
+                               const double* T, int n, double tol, int maxit, int precision,
+                               double* feq, double* lambda, int* iters, int* status,
+                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  equilibrium_kernel<<<(n + 127) / 128, 128, 0, s>>>(rho, ubx, uby, T, n, tol, maxit, feq, lambda,
-                                                     iters, status);
+  equilibrium_kernel<<<(n + 127) / 128, 128, 0, s>>>(rho, ubx, uby, T, n, tol, maxit, precision,
+                                                     feq, lambda, iters, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  exp_neg_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, n, out);
   return cudaGetLastError();
 }
 

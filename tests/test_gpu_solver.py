@@ -1,0 +1,105 @@
+"""The FP32 form's equilibrium solver and its FP64 exponential, through the C ABI.
+
+* alb_equilibrium with ALB_FP32_FORM (FP32 Newton refined with FP64
+  residuals) against the CPU oracle on 10^4 states: 1e-10 relative, the same
+  convergence decision, and few FP64 evaluations per state.
+* alb_exp_neg (table-driven FP64 exponential, Tang's method) against CUDA's
+  own exp: a few ulp.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def alb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_13426_gb300 import alb as A
+    A.lib()
+    return A
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(a, dtype=dtype, device="cuda")
+
+
+def _sweep(alb, rho, ubx, uby, T, precision):
+    n = rho.size
+    feq = torch.empty(n * 21, dtype=torch.float64, device="cuda")
+    its = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    alb.alb_equilibrium(_dev(rho), _dev(ubx), _dev(uby), _dev(T), n, 1e-12, 50, feq, None, its,
+                        st, precision=precision)
+    torch.cuda.synchronize()
+    return feq.cpu().numpy().reshape(n, 21), its.cpu().numpy(), st.cpu().numpy()
+
+
+def test_mixed_solver_matches_oracle(alb):
+    rng = np.random.default_rng(22)
+    n = 10000
+    rho = rng.uniform(0.05, 4.0, n)
+    ang = rng.uniform(0, 2 * np.pi, n)
+    mag = rng.uniform(0, 1.5, n)
+    T = rng.uniform(0.3, 1.5, n)
+    ubx, uby = mag * np.cos(ang), mag * np.sin(ang)
+    feq, evals, st = _sweep(alb, rho, ubx, uby, T, alb.ALB_FP32_FORM)
+    for k in range(n):
+        ost, olam, ofeq, oit = O.equilibrium(rho[k], ubx[k], uby[k], T[k])
+        assert (ost == O.OK) == (st[k] == 0), (k, rho[k], ubx[k], uby[k], T[k], ost, st[k])
+        if ost == O.OK:
+            # Both stop at max|G|/rho <= 1e-12, the refinement as soon as it is met
+            # (near 1e-13), the oracle's Newton usually well below it; populations
+            # agree to the criterion's sensitivity, not to round-off.
+            np.testing.assert_allclose(feq[k], ofeq, rtol=1e-10, atol=2e-12 * rho[k])
+    ok = st == 0
+    # FP64 work: the refinement needs a few residual evaluations per state
+    assert np.mean(evals[ok]) <= 4.0, np.mean(evals[ok])
+
+
+def test_mixed_solver_reaches_the_criterion(alb):
+    """Constraint residuals of the returned equilibria, recomputed on the host
+    from Eqs. G0_8mom..G3yaa_8mom, are below the 1e-12 criterion."""
+    rng = np.random.default_rng(5)
+    n = 2000
+    rho = rng.uniform(0.1, 2.0, n)
+    ubx = rng.uniform(-0.7, 0.7, n)
+    uby = rng.uniform(-0.7, 0.7, n)
+    T = rng.uniform(0.35, 1.2, n)
+    feq, _, st = _sweep(alb, rho, ubx, uby, T, alb.ALB_FP32_FORM)
+    assert (st == 0).all()
+    x, y = O.velocities()
+    x = x.astype(float)
+    y = y.astype(float)
+    r2 = x * x + y * y
+    P = np.stack([np.ones(21), x, y, x * x, x * y, y * y, x * r2, y * r2])
+    for k in range(n):
+        m = O.targets(rho[k], ubx[k], uby[k], T[k])
+        assert np.abs(P @ feq[k] - m).max() / rho[k] <= 1.5e-12
+
+
+def test_table_exponential_against_cuda_exp(alb):
+    rng = np.random.default_rng(8)
+    s = np.concatenate([rng.uniform(-30, 60, 400000), rng.uniform(-690, 690, 100000),
+                        np.arange(-64, 64) * np.log(2) / 32, [0.0, 1.0, -1.0, 700.0, -700.0]])
+    n = s.size
+    sd = _dev(s)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    alb.alb_exp_neg(sd, n, out)
+    ref = torch.exp(-sd)  # CUDA's own FP64 exp
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = ref.cpu().numpy()
+    rel = np.abs(got - ref) / ref
+    assert rel.max() <= 4 * 2.0 ** -52, rel.max()
+    # limits: 0 far below, +inf far above the double range
+    t = _dev([1000.0, -1000.0])
+    o = torch.empty(2, dtype=torch.float64, device="cuda")
+    alb.alb_exp_neg(t, 2, o)
+    torch.cuda.synchronize()
+    o = o.cpu().numpy()
+    assert o[0] == 0.0 and np.isinf(o[1])
