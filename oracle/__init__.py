@@ -70,6 +70,8 @@ def lib():
         L.ora_init.restype = ctypes.c_int
         L.ora_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.ora_step.restype = ctypes.c_int
+        L.ora_step_forced.argtypes = [ctypes.c_void_p, _bp, _bp]
+        L.ora_step_forced.restype = ctypes.c_int
         L.ora_get_moments.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
         L.ora_get_primitives.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
         L.ora_get_shifts.argtypes = [ctypes.c_void_p, _bp, _bp]
@@ -166,6 +168,11 @@ class Simulation:
 
     def step(self, n):
         return lib().ora_step(self._h, int(n))
+
+    def step_forced(self, ux, uy):
+        """One step pulling into the given lattices (arrays (ny, nx) of shifts)."""
+        return lib().ora_step_forced(self._h, np.ascontiguousarray(ux, np.int8).reshape(-1),
+                                     np.ascontiguousarray(uy, np.int8).reshape(-1))
 
     def moments(self):
         n = self.nx * self.ny

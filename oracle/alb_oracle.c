@@ -479,11 +479,13 @@ static void rebuild_fallback(ora_state* s, int i, int Upx, int Upy, int sx, int 
   *gi = (2.0 * Cv - D_SPACE) * s->T[k] * (*fi);
 }
 
-int ora_step(ora_state* s, int nsteps) {
+/* One time iteration; if forced_x / forced_y are given they replace the
+ * criterion's choice of the next lattice (replay of recorded decisions). */
+static int step_once(ora_state* s, const signed char* forced_x, const signed char* forced_y) {
   const ora_config* c = &s->cfg;
   const int nx = c->nx, ny = c->ny;
   int status = ORA_OK;
-  for (int step = 0; step < nsteps; ++step) {
+  {
     /* (i) moments, equilibrium, collision, next shift: every node in its own lattice */
     long long fails = 0, calls = 0;
 #pragma omp parallel for reduction(+ : fails, calls) schedule(static)
@@ -497,8 +499,13 @@ int ora_step(ora_state* s, int nsteps) {
                                 &s->gs[(size_t)k * ORA_Q]);
       calls += 1;
       if (st != ORA_OK) fails += 1;
-      s->Unx[k] = (signed char)ora_select_shift(mom[1], c->n0, c->umax);
-      s->Uny[k] = (signed char)ora_select_shift(mom[2], c->n0, c->umax);
+      if (forced_x) {
+        s->Unx[k] = forced_x[k];
+        s->Uny[k] = forced_y[k];
+      } else {
+        s->Unx[k] = (signed char)ora_select_shift(mom[1], c->n0, c->umax);
+        s->Uny[k] = (signed char)ora_select_shift(mom[2], c->n0, c->umax);
+      }
     }
     s->stats.newton_calls += calls;
     s->stats.newton_failures += fails;
@@ -541,6 +548,23 @@ int ora_step(ora_state* s, int nsteps) {
     memcpy(s->Uy, s->Uny, (size_t)s->n);
   }
   return status;
+}
+
+int ora_step(ora_state* s, int nsteps) {
+  int status = ORA_OK;
+  for (int step = 0; step < nsteps; ++step) {
+    const int st = step_once(s, NULL, NULL);
+    if (st != ORA_OK) status = st;
+  }
+  return status;
+}
+
+int ora_step_forced(ora_state* s, const signed char* ux, const signed char* uy) {
+  for (int k = 0; k < s->n; ++k)
+    if (ux[k] < -s->cfg.umax || ux[k] > s->cfg.umax || uy[k] < -s->cfg.umax ||
+        uy[k] > s->cfg.umax)
+      return ORA_EINVAL;
+  return step_once(s, ux, uy);
 }
 
 void ora_get_primitives(const ora_state* s, double* rho, double* ux, double* uy, double* T) {

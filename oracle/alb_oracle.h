@@ -111,6 +111,13 @@ int ora_init(ora_state* s, const double* rho, const double* rhoux, const double*
  * failed (state stays valid, failures are counted). */
 int ora_step(ora_state* s, int nsteps);
 
+/* One time iteration in which the lattice each node pulls into is given
+ * (ux, uy: nx*ny shifts within +-umax) instead of chosen by Eq. criterion;
+ * everything else as ora_step. Replays lattice decisions recorded from
+ * another implementation, so that arithmetic differences can be compared
+ * without the discontinuity of a threshold decision taken differently. */
+int ora_step_forced(ora_state* s, const signed char* ux, const signed char* uy);
+
 /* Conserved moments of the current (pre-collision) populations. */
 void ora_get_moments(const ora_state* s, double* rho, double* rhoux, double* rhouy,
                      double* rhoE);

@@ -169,6 +169,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.sky[1] = cfg->sensor_alpha[0];
   p.sky[2] = cfg->sensor_alpha[1];
   p.sky[3] = cfg->sensor_alpha[2];
+  for (int t = 0; t < 6; ++t) p.thr[t] = (double)(t - cfg->u_max + 1) - cfg->n0;
   d.precision = cfg->precision;
   d.n = (size_t)cfg->nx * cfg->ny;
   d.ps = (d.n + 63) / 64 * 64;

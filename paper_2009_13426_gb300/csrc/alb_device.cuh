@@ -53,7 +53,18 @@ struct Params {
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
   double seps[3], salpha[3];
   double skx[4], sky[4];  // sensor knots: log10(eps) and alpha (host-computed)
+  double thr[6];          // criterion thresholds (t + 1) - n0, t = -umax .. umax - 1
 };
+
+// Eq. criterion with the host-computed thresholds of Params (the same IEEE
+// values as select_shift computes).
+__device__ __forceinline__ int select_shift_thr(double u, const Params& pr) {
+  int n = -pr.umax;
+#pragma unroll
+  for (int t = 0; t < 6; ++t)
+    if (t < 2 * pr.umax && u > pr.thr[t]) ++n;
+  return n;
+}
 
 // s + c * v with c a compile-time integer after unrolling: the zero and unit
 // cases fold away, keeping IEEE semantics for the rest.

@@ -2,261 +2,22 @@
 //
 //  step_kernel   pull (Eq. stream) in the receiver's lattice with Grad rebuild
 //                of missing pulls (Eqs. GradGeneral*), moments (Eq. polyTemp),
-//                shift for the next pull (Eq. criterion), FP64 Newton for the
-//                numerical equilibrium (Eq. feqNum_8Mom), g^eq (Eq. gEq),
-//                optional sensor (Eq. DeltaAvg), BGK (Eq. coll), store.
+//                shift for the next pull (Eq. criterion), numerical equilibrium
+//                (Eq. feqNum_8Mom), g^eq (Eq. gEq), optional sensor
+//                (Eq. DeltaAvg), BGK (Eq. coll), store.
 //  init_kernel   Grad-regularised initial populations, then the same collision.
 //  export / equilibrium / select kernels for the C ABI.
 //
 // Layout: structure of arrays. Plane p (f_0..f_20, g_0..g_20) of a buffer is
 // a contiguous nx*ny array, x fastest; lattice codes and moments likewise.
+// Each thread owns two columns of the block's dynamic shared memory: its 42
+// pulled populations (stride BLOCK) and the 21 FP64 equilibrium values per
+// unit density of its latest equilibrium solve (stride BLOCK).
 #include <type_traits>
 
-#include "alb_internal.h"
-#include "alb_mixed.cuh"
+#include "alb_step.cuh"
 
 namespace alb {
-
-constexpr int BLOCK = 128;
-
-// Equilibrium of one node in the storage precision P: the full FP64 Newton for
-// the FP64 plain path, the mixed FP32/FP64 solver for the FP32 form.
-template <typename P>
-__device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, double uby,
-                                                double T, const double* tab, const float* warm,
-                                                double lam[NM], double p[Q], SolveCount* cnt) {
-  if constexpr (std::is_same<P, float>::value) {
-    return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, lam, p, cnt);
-  } else {
-    int it = 0, ev = 0;
-    const int st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev);
-    cnt->fp64_iters += it;
-    cnt->fp64_evals += ev;
-    return st;
-  }
-}
-
-// exp(-(1 + lambda . P(xi))) for one velocity (cx, cy) given at run time.
-template <typename P>
-__device__ __forceinline__ double p_one(const double lam[NM], int cx, int cy, const double* tab) {
-  if constexpr (std::is_same<P, float>::value) {
-    const double x = cx, y = cy, r2 = x * x + y * y;
-    double s = 1.0 + lam[0];
-    s = fma(lam[1], x, s);
-    s = fma(lam[2], y, s);
-    s = fma(lam[3], x * x, s);
-    s = fma(lam[4], x * y, s);
-    s = fma(lam[5], y * y, s);
-    s = fma(lam[6], x * r2, s);
-    s = fma(lam[7], y * r2, s);
-    return exp_neg(s, tab);
-  } else {
-    return exp_family_one(lam, cx, cy);
-  }
-}
-
-// Moment accumulation: plain in FP64; Neumaier-compensated in FP32.
-template <typename P>
-struct Acc {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double v) { s += v; }
-  __device__ __forceinline__ double val() const { return s; }
-};
-template <>
-struct Acc<float> {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float v) {
-    const float t = s + v;
-    if (fabsf(s) >= fabsf(v))
-      c += (s - t) + v;
-    else
-      c += (v - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ double val() const { return (double)(s + c); }
-};
-
-template <typename P>
-struct StepArgs {
-  const P* pop_in;
-  P* pop_out;
-  const P* mom_in;
-  P* mom_out;
-  const uint8_t* lat_in;
-  const uint8_t* nxt_in;
-  uint8_t* lat_out;
-  uint8_t* nxt_out;
-  const float* lam_in;  // FP32 form: multipliers of the previous step (8 planes)
-  float* lam_out;
-  size_t ps;
-  Params prm;
-  unsigned long long* ctr;
-};
-
-// Multipliers stored for node k (8 planes), moved into the frame of lattice
-// (Ux, Uy) from the lattice code they were computed in.
-__device__ __forceinline__ void load_warm(const float* lam, size_t ps, size_t k, int code_from,
-                                          int Ux, int Uy, float w[NM]) {
-  float l[NM];
-#pragma unroll
-  for (int j = 0; j < NM; ++j) l[j] = lam[j * ps + k];
-  const int dx = lat_ux(code_from) - Ux, dy = lat_uy(code_from) - Uy;
-  if (dx == 0 && dy == 0) {
-#pragma unroll
-    for (int j = 0; j < NM; ++j) w[j] = l[j];
-  } else {
-    shift_multipliers(l, (float)dx, (float)dy, w);
-  }
-}
-
-// Grad rebuild of a missing pull (Sec. III.B.2, IV.A.3): the post-collision
-// population of velocity (cx, cy) in the receiver's lattice (Upx, Upy), built
-// from the sender's moments at (sx, sy) (possibly a ghost), their central
-// differences and the sender's relaxation time: h* = h^eq (1 + (1 - 1/tau) phi_h).
-// Returns 1 if the root finder failed and the Maxwellian-guess fallback was used.
-template <typename P>
-__device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
-                                         int cx, int cy, int Upx, int Upy, int sx, int sy,
-                                         double* fi, double* gi, const double* tab,
-                                         const float* lam_in, const uint8_t* lat_in,
-                                         SolveCount* cnt) {
-  bool gh = false;
-  const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
-  const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
-  const int xp = resolve(sx + 1, pr.nx, pr.bcx, &gh);
-  const int xm = resolve(sx - 1, pr.nx, pr.bcx, &gh);
-  const int yp = resolve(sy + 1, pr.ny, pr.bcy, &gh);
-  const int ym = resolve(sy - 1, pr.ny, pr.bcy, &gh);
-  const size_t nx = (size_t)pr.nx;
-  const size_t ks = ry * nx + rx;
-  const size_t kxp = ry * nx + xp, kxm = ry * nx + xm, kyp = yp * nx + rx, kym = ym * nx + rx;
-  const P* mr = mom;
-  const P* mux = mom + ps;
-  const P* muy = mom + 2 * ps;
-  const P* mT = mom + 3 * ps;
-  const double rho = (double)mr[ks], ux = (double)mux[ks], uy = (double)muy[ks],
-               T = (double)mT[ks];
-  double du[2][2], dT[2];
-  du[0][0] = 0.5 * ((double)mux[kxp] - (double)mux[kxm]);
-  du[1][0] = 0.5 * ((double)mux[kyp] - (double)mux[kym]);
-  du[0][1] = 0.5 * ((double)muy[kxp] - (double)muy[kxm]);
-  du[1][1] = 0.5 * ((double)muy[kyp] - (double)muy[kym]);
-  dT[0] = 0.5 * ((double)mT[kxp] - (double)mT[kxm]);
-  dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
-  const double ubx = ux - Upx, uby = uy - Upy;
-  double lam[NM], p[Q];
-  float wbuf[NM];
-  const float* warm = nullptr;
-  if constexpr (std::is_same<P, float>::value) {
-    load_warm(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
-    warm = wbuf;
-  }
-  const int st = (rho > 0.0) ? node_equilibrium<P>(pr, ubx, uby, T, tab, warm, lam, p, cnt)
-                             : NEWTON_UNREALIZABLE;
-  const double gfac = (2.0 * pr.cv - 2.0) * T;
-  if (st != NEWTON_OK) {
-    if (T > 0.0) {
-      maxwellian_guess(ubx, uby, T, lam);
-      *fi = rho * exp_family_one(lam, cx, cy);
-    } else {
-      *fi = 0.0;
-    }
-    *gi = gfac * (*fi);
-    return 1;
-  }
-  const double tau = 0.5 + pr.nu / T;
-  const double omega = 1.0 - 1.0 / tau;
-  const double feq = rho * p_one<P>(lam, cx, cy, tab);
-  const double cbx = (double)(cx + Upx) - ux;
-  const double cby = (double)(cy + Upy) - uy;
-  double phf, phg;
-  grad_phi(pr, rho, T, cbx, cby, du, dT, &phf, &phg);
-  *fi = feq * (1.0 + omega * phf);
-  *gi = gfac * feq * (1.0 + omega * phg);
-  return 0;
-}
-
-// Moments, next shift, equilibrium and BGK of one node whose 42 pre-collision
-// populations sit in the shared stash (column of this thread), then store.
-template <typename P>
-__device__ __forceinline__ void collide_store(const Params& pr, const P* st, int code, size_t k,
-                                              size_t ps, P* __restrict__ pop_out,
-                                              P* __restrict__ mom_out, uint8_t* lat_out,
-                                              uint8_t* nxt_out, const double* tab,
-                                              const float* warm, float* lam_out,
-                                              SolveCount* cnt, unsigned* n_fail) {
-  const int Ux = lat_ux(code), Uy = lat_uy(code);
-  Acc<P> ar, ajx, ajy, ae;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const P f = st[i * BLOCK];
-    const P g = st[(Q + i) * BLOCK];
-    constexpr int dummy = 0;
-    (void)dummy;
-    ar.add(f);
-    if (XI_X(i) != 0) ajx.add(XI_X(i) == 1 ? f : XI_X(i) == -1 ? -f : (P)XI_X(i) * f);
-    if (XI_Y(i) != 0) ajy.add(XI_Y(i) == 1 ? f : XI_Y(i) == -1 ? -f : (P)XI_Y(i) * f);
-    const int c2 = XI_X(i) * XI_X(i) + XI_Y(i) * XI_Y(i);
-    if (c2 != 0) ae.add(c2 == 1 ? f : (P)c2 * f);
-    ae.add(g);
-  }
-  const double rho = ar.val();
-  const double ubx = ajx.val() / rho, uby = ajy.val() / rho;
-  const double T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
-  const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
-  const int code2 = lat_code(select_shift(ux, pr.n0, pr.umax), select_shift(uy, pr.n0, pr.umax));
-
-  double lam[NM], p[Q];
-  const int ns = (rho > 0.0) ? node_equilibrium<P>(pr, ubx, uby, T, tab, warm, lam, p, cnt)
-                             : NEWTON_UNREALIZABLE;
-  if constexpr (std::is_same<P, float>::value) {
-    // multipliers for the next step's warm start (lattice `code`)
-    if (ns == NEWTON_OK) {
-#pragma unroll
-      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = (float)lam[j];
-    } else if (warm) {
-#pragma unroll
-      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = warm[j];
-    } else {
-#pragma unroll
-      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = j == 3 || j == 5 ? 0.5f : 0.0f;
-    }
-  }
-  if (ns == NEWTON_OK) {
-    const double gfac = (2.0 * pr.cv - 2.0) * T;
-    double tau = 0.5 + pr.nu / T;
-    if (pr.sensor) {
-      P eps = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const P fe = (P)(rho * p[i]);
-        eps += fabs(st[i * BLOCK] - fe) / fe;
-      }
-      eps /= (P)Q;
-      tau *= (double)sensor_alpha<P>(pr, eps);
-    }
-    const P om = (P)(1.0 / tau);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const P fe = (P)(rho * p[i]);
-      const P ge = (P)(gfac * rho * p[i]);
-      const P f = st[i * BLOCK];
-      const P g = st[(Q + i) * BLOCK];
-      pop_out[i * ps + k] = fma(om, fe - f, f);
-      pop_out[(Q + i) * ps + k] = fma(om, ge - g, g);
-    }
-  } else {
-    *n_fail += 1;
-#pragma unroll
-    for (int i = 0; i < NPLANES; ++i) pop_out[i * ps + k] = st[i * BLOCK];
-  }
-  mom_out[k] = (P)rho;
-  mom_out[ps + k] = (P)ux;
-  mom_out[2 * ps + k] = (P)uy;
-  mom_out[3 * ps + k] = (P)T;
-  lat_out[k] = (uint8_t)code;
-  nxt_out[k] = (uint8_t)code2;
-}
 
 template <typename P>
 __global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1))
@@ -264,57 +25,12 @@ __global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_tab[32];
   load_exptab(s_tab);
-  P* st = reinterpret_cast<P*>(smem_raw) + threadIdx.x;
-  const Params& pr = a.prm;
+  const Columns<P, BLOCK> cl(smem_raw);
   const int x = blockIdx.x * BLOCK + threadIdx.x;
   const int y = blockIdx.y;
-  unsigned n_rec = 0, n_rec_fail = 0, n_fail = 0, n_calls = 0;
-  SolveCount cnt;
-  if (x < pr.nx) {
-    const size_t k = (size_t)y * pr.nx + x;
-    const size_t ps = a.ps;
-    const int code = a.nxt_in[k];
-    const int Upx = lat_ux(code), Upy = lat_uy(code);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int sx = x - XI_X(i) - Upx;
-      const int sy = y - XI_Y(i) - Upy;
-      bool gh = false;
-      const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
-      const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
-      const size_t ks = (size_t)ry * pr.nx + rx;
-      P fi, gi;
-      if (!gh && a.lat_in[ks] == code) {
-        fi = a.pop_in[i * ps + ks];
-        gi = a.pop_in[(Q + i) * ps + ks];
-      } else {
-        double fd, gd;
-        n_rec += 1;
-        n_rec_fail += rebuild_pull<P>(pr, a.mom_in, ps, XI_X(i), XI_Y(i), Upx, Upy, sx, sy, &fd,
-                                      &gd, s_tab, a.lam_in, a.lat_in, &cnt);
-        fi = (P)fd;
-        gi = (P)gd;
-      }
-      st[i * BLOCK] = fi;
-      st[(Q + i) * BLOCK] = gi;
-    }
-    float wbuf[NM];
-    const float* warm = nullptr;
-    if constexpr (std::is_same<P, float>::value) {
-      load_warm(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
-      warm = wbuf;
-    }
-    collide_store<P>(pr, st, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,
-                     warm, a.lam_out, &cnt, &n_fail);
-    n_calls = 1 + n_rec;
-  }
-  warp_count(a.ctr + CTR_NEWTON_ITERS, cnt.fp64_iters);
-  warp_count(a.ctr + CTR_FP64_EVALS, cnt.fp64_evals);
-  warp_count(a.ctr + CTR_FP32_ITERS, cnt.fp32_iters);
-  warp_count(a.ctr + CTR_NEWTON_CALLS, n_calls);
-  warp_count(a.ctr + CTR_NEWTON_FAIL, n_fail);
-  warp_count(a.ctr + CTR_REC, n_rec);
-  warp_count(a.ctr + CTR_REC_FAIL, n_rec_fail);
+  NodeCount nc;
+  if (x < a.prm.nx) node_step<P, BLOCK>(a, x, y, cl, s_tab, nc);
+  flush_counts(a.ctr, nc);
 }
 
 template <typename P>
@@ -347,7 +63,7 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_tab[32];
   load_exptab(s_tab);
-  P* st = reinterpret_cast<P*>(smem_raw) + threadIdx.x;
+  const Columns<P, BLOCK> cl(smem_raw);
   const Params& pr = a.prm;
   const int x = blockIdx.x * BLOCK + threadIdx.x;
   const int y = blockIdx.y;
@@ -374,11 +90,11 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
     dT[1] = 0.5 * (T1 - T2);
     const int U0x = select_shift(ux, pr.n0, pr.umax), U0y = select_shift(uy, pr.n0, pr.umax);
     const int code = lat_code(U0x, U0y);
-    double lam[NM], p[Q];
+    double lam[NM];
     const bool realizable = (r > 0.0) && (T > 0.0) && isfinite(r) && isfinite(T);
-    const int ns = realizable
-                       ? node_equilibrium<P>(pr, ux - U0x, uy - U0y, T, s_tab, nullptr, lam, p, &cnt)
-                       : NEWTON_UNREALIZABLE;
+    const int ns = realizable ? node_equilibrium<P>(pr, ux - U0x, uy - U0y, T, s_tab, nullptr,
+                                                    cl.eq, lam, &cnt)
+                              : NEWTON_UNREALIZABLE;
     if (!realizable) n_bad += 1;
     if (ns != NEWTON_OK && realizable) n_fail += 1;
     const double gfac = (2.0 * pr.cv - 2.0) * T;
@@ -390,10 +106,10 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
       double feq = 0.0;
       if (ns == NEWTON_OK) {
         grad_phi(pr, r, T, cbx, cby, du, dT, &phf, &phg);
-        feq = r * p[i];
+        feq = r * cl.eq[i * BLOCK];
       }
-      st[i * BLOCK] = (P)(feq * (1.0 + phf));
-      st[(Q + i) * BLOCK] = (P)(gfac * feq * (1.0 + phg));
+      cl.pop[i * BLOCK] = (P)(feq * (1.0 + phf));
+      cl.pop[(Q + i) * BLOCK] = (P)(gfac * feq * (1.0 + phg));
     }
     if (ns == NEWTON_OK) {
       float wbuf[NM];
@@ -403,8 +119,8 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
         for (int j = 0; j < NM; ++j) wbuf[j] = (float)lam[j];
         warm = wbuf;
       }
-      collide_store<P>(pr, st, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out,
-                       s_tab, warm, a.lam_out, &cnt, &n_fail);
+      collide_store<P, BLOCK>(pr, cl, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out,
+                              s_tab, warm, a.lam_out, &cnt, &n_fail);
     } else {
       for (int i = 0; i < NPLANES; ++i) a.pop_out[i * a.ps + k] = (P)0;
       a.mom_out[k] = (P)r;
@@ -446,14 +162,17 @@ __global__ void export_shifts_kernel(const uint8_t* lat, size_t n, signed char* 
   }
 }
 
-__global__ void equilibrium_kernel(const double* rho, const double* ubx, const double* uby,
-                                   const double* T, int n, double tol, int maxit, int precision,
-                                   double* feq, double* lambda, int* iters, int* status) {
+__global__ void __launch_bounds__(BLOCK)
+    equilibrium_kernel(const double* rho, const double* ubx, const double* uby, const double* T,
+                       int n, double tol, int maxit, int precision, double* feq, double* lambda,
+                       int* iters, int* status) {
   __shared__ double s_tab[32];
+  __shared__ double s_eq[Q * BLOCK];
   load_exptab(s_tab);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  double lam[NM], p[Q];
+  double* eq = s_eq + threadIdx.x;
+  double lam[NM];
   const double r = rho[k];
   Params pr{};
   pr.tol = tol;
@@ -462,10 +181,9 @@ __global__ void equilibrium_kernel(const double* rho, const double* ubx, const d
   int st = NEWTON_UNREALIZABLE;
   if (r > 0.0)
     st = precision == 0
-             ? node_equilibrium<double>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, lam, p, &cnt)
-             : node_equilibrium<float>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, lam, p, &cnt);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) feq[(size_t)k * Q + i] = r * p[i];
+             ? node_equilibrium<double>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, eq, lam, &cnt)
+             : node_equilibrium<float>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, eq, lam, &cnt);
+  for (int i = 0; i < Q; ++i) feq[(size_t)k * Q + i] = st == NEWTON_UNREALIZABLE ? 0.0 : r * eq[i * BLOCK];
   if (lambda)
 #pragma unroll
     for (int j = 0; j < NM; ++j) lambda[(size_t)k * NM + j] = lam[j];
@@ -491,35 +209,48 @@ __global__ void select_kernel(const double* rho, const double* rhou, int n, doub
 
 static dim3 grid_of(const Params& p) { return dim3((p.nx + BLOCK - 1) / BLOCK, p.ny); }
 
+// Dynamic shared memory above 48 KB needs an explicit opt-in per kernel.
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, const double* rhouy,
                         const double* rhoE, cudaStream_t s) {
   const int out = f.cur;
+  cudaError_t e;
   if (f.precision == 0) {
     InitArgs<double> a{rho, rhoux, rhouy, rhoE, (double*)f.pop[out], (double*)f.mom[out],
                        f.lat[out], f.nxt[out], nullptr, f.ps, f.prm, f.ctr};
-    init_kernel<double><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(double), s>>>(a);
+    if ((e = allow_smem(init_kernel<double>, smem_bytes<double>())) != cudaSuccess) return e;
+    init_kernel<double><<<grid_of(f.prm), BLOCK, smem_bytes<double>(), s>>>(a);
   } else {
     InitArgs<float> a{rho, rhoux, rhouy, rhoE, (float*)f.pop[out], (float*)f.mom[out],
                       f.lat[out], f.nxt[out], f.lam[out], f.ps, f.prm, f.ctr};
-    init_kernel<float><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(float), s>>>(a);
+    if ((e = allow_smem(init_kernel<float>, smem_bytes<float>())) != cudaSuccess) return e;
+    init_kernel<float><<<grid_of(f.prm), BLOCK, smem_bytes<float>(), s>>>(a);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_step(FlowDev& f, cudaStream_t s) {
   const int in = f.cur, out = f.cur ^ 1;
+  cudaError_t e;
   if (f.precision == 0) {
     StepArgs<double> a{(const double*)f.pop[in], (double*)f.pop[out], (const double*)f.mom[in],
                        (double*)f.mom[out], f.lat[in], f.nxt[in], f.lat[out], f.nxt[out],
                        nullptr, nullptr, f.ps, f.prm, f.ctr};
-    step_kernel<double><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(double), s>>>(a);
+    if ((e = allow_smem(step_kernel<double>, smem_bytes<double>())) != cudaSuccess) return e;
+    step_kernel<double><<<grid_of(f.prm), BLOCK, smem_bytes<double>(), s>>>(a);
   } else {
     StepArgs<float> a{(const float*)f.pop[in], (float*)f.pop[out], (const float*)f.mom[in],
                       (float*)f.mom[out], f.lat[in], f.nxt[in], f.lat[out], f.nxt[out],
                       f.lam[in], f.lam[out], f.ps, f.prm, f.ctr};
-    step_kernel<float><<<grid_of(f.prm), BLOCK, NPLANES * BLOCK * sizeof(float), s>>>(a);
+    if ((e = allow_smem(step_kernel<float>, smem_bytes<float>())) != cudaSuccess) return e;
+    step_kernel<float><<<grid_of(f.prm), BLOCK, smem_bytes<float>(), s>>>(a);
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) f.cur = out;
   return e;
 }
@@ -548,8 +279,9 @@ cudaError_t launch_equilibrium(const double* rho, const double* ubx, const doubl
                                double* feq, double* lambda, int* iters, int* status,
                                cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  equilibrium_kernel<<<(n + 127) / 128, 128, 0, s>>>(rho, ubx, uby, T, n, tol, maxit, precision,
-                                                     feq, lambda, iters, status);
+  equilibrium_kernel<<<(n + BLOCK - 1) / BLOCK, BLOCK, 0, s>>>(rho, ubx, uby, T, n, tol, maxit,
+                                                               precision, feq, lambda, iters,
+                                                               status);
   return cudaGetLastError();
 }
 

@@ -15,9 +15,12 @@
 // 2^(j/32) from a 32-entry table and exp(r) by its degree-6 Taylor polynomial
 // (constants in exp_table.h, generated by gen_exp_table.py).
 //
-// Exponents and constraint sums use the symmetry of the velocity set: for each
-// pair (or quadruple) of velocities related by a sign change, the sum and
-// difference (butterfly) are formed once and shared by all moments.
+// Every pass over the velocities streams through the symmetric groups of the
+// D2Q21 set (the rest velocity, the axis pairs +-a, the diagonal quadruples):
+// a group's exponents are built from shared even and odd parts, exponentiated
+// and folded into the sums at once, so no per-velocity array stays live. The
+// FP64 constraint sums use the butterfly of each group (sums and differences
+// formed once for all moments).
 #pragma once
 
 #include "alb_device.cuh"
@@ -25,35 +28,30 @@
 
 namespace alb {
 
-// Exponents s_i = 1 + lambda . P(xi_i) for the 21 velocities (index order of
-// XI_X / XI_Y), built from the even and odd parts of each symmetric group.
-template <typename R>
-__device__ __forceinline__ void exponents(const R l[NM], R s[Q]) {
+// Calls v.rest(s_0), v.pair<a, axis, i+, i->(s_+, s_-) and
+// v.quad<a, i++, i-+, i--, i+->(...) with the exponents
+// s_i = 1 + lambda . P(xi_i) of every group (index order of XI_X / XI_Y).
+template <typename R, typename V>
+__device__ __forceinline__ void visit_groups(const R l[NM], V& v) {
   const R c = (R)1 + l[0];
-  s[0] = c;
+  v.rest(c);
   {  // axis, |xi| = 1
     const R ex = c + l[3], ox = l[1] + l[6];
-    s[1] = ex + ox;
-    s[3] = ex - ox;
+    v.template pair<1, 0, 1, 3>(ex + ox, ex - ox);
     const R ey = c + l[5], oy = l[2] + l[7];
-    s[2] = ey + oy;
-    s[4] = ey - oy;
+    v.template pair<1, 1, 2, 4>(ey + oy, ey - oy);
   }
   {  // axis, |xi| = 2
     const R ex = fma((R)4, l[3], c), ox = fma((R)8, l[6], (R)2 * l[1]);
-    s[9] = ex + ox;
-    s[11] = ex - ox;
+    v.template pair<2, 0, 9, 11>(ex + ox, ex - ox);
     const R ey = fma((R)4, l[5], c), oy = fma((R)8, l[7], (R)2 * l[2]);
-    s[10] = ey + oy;
-    s[12] = ey - oy;
+    v.template pair<2, 1, 10, 12>(ey + oy, ey - oy);
   }
   {  // axis, |xi| = 3
     const R ex = fma((R)9, l[3], c), ox = fma((R)27, l[6], (R)3 * l[1]);
-    s[17] = ex + ox;
-    s[19] = ex - ox;
+    v.template pair<3, 0, 17, 19>(ex + ox, ex - ox);
     const R ey = fma((R)9, l[5], c), oy = fma((R)27, l[7], (R)3 * l[2]);
-    s[18] = ey + oy;
-    s[20] = ey - oy;
+    v.template pair<3, 1, 18, 20>(ey + oy, ey - oy);
   }
   const R l35 = l[3] + l[5];
   {  // diagonal (+-1, +-1): s = E + sx sy Z + sx X + sy Y
@@ -61,10 +59,7 @@ __device__ __forceinline__ void exponents(const R l[NM], R s[Q]) {
     const R X = fma((R)2, l[6], l[1]), Y = fma((R)2, l[7], l[2]);
     const R Ep = E + l[4], Em = E - l[4];
     const R XpY = X + Y, XmY = X - Y;
-    s[5] = Ep + XpY;  // ( 1, 1)
-    s[7] = Ep - XpY;  // (-1,-1)
-    s[8] = Em + XmY;  // ( 1,-1)
-    s[6] = Em - XmY;  // (-1, 1)
+    v.template quad<1, 5, 6, 7, 8>(Ep + XpY, Em - XmY, Ep - XpY, Em + XmY);
   }
   {  // diagonal (+-2, +-2)
     const R E = fma((R)4, l35, c);
@@ -72,51 +67,8 @@ __device__ __forceinline__ void exponents(const R l[NM], R s[Q]) {
     const R Z = (R)4 * l[4];
     const R Ep = E + Z, Em = E - Z;
     const R XpY = X + Y, XmY = X - Y;
-    s[13] = Ep + XpY;  // ( 2, 2)
-    s[15] = Ep - XpY;  // (-2,-2)
-    s[16] = Em + XmY;  // ( 2,-2)
-    s[14] = Em - XmY;  // (-2, 2)
+    v.template quad<2, 13, 14, 15, 16>(Ep + XpY, Em - XmY, Ep - XpY, Em + XmY);
   }
-}
-
-// The 8 constraint moments M_k = sum_i p_i P_k(xi_i) (Eq. 8moments order).
-template <typename R>
-__device__ __forceinline__ void moments8(const R p[Q], R M[NM]) {
-  R m0 = p[0], m1 = 0, m2 = 0, m3 = 0, m4 = 0, m5 = 0, m6 = 0, m7 = 0;
-  // axis pairs (+a, -a) along x and y, a = 1, 2, 3
-  const int ax[3][2] = {{1, 3}, {9, 11}, {17, 19}};
-  const int ay[3][2] = {{2, 4}, {10, 12}, {18, 20}};
-#pragma unroll
-  for (int a = 1; a <= 3; ++a) {
-    const R Sx = p[ax[a - 1][0]] + p[ax[a - 1][1]], Dx = p[ax[a - 1][0]] - p[ax[a - 1][1]];
-    const R Sy = p[ay[a - 1][0]] + p[ay[a - 1][1]], Dy = p[ay[a - 1][0]] - p[ay[a - 1][1]];
-    m0 += Sx + Sy;
-    m1 = madd(m1, Dx, a);
-    m2 = madd(m2, Dy, a);
-    m3 = madd(m3, Sx, a * a);
-    m5 = madd(m5, Sy, a * a);
-    m6 = madd(m6, Dx, a * a * a);
-    m7 = madd(m7, Dy, a * a * a);
-  }
-  // diagonal quadruples (a,a), (a,-a), (-a,a), (-a,-a), a = 1, 2
-  const int dg[2][4] = {{5, 8, 6, 7}, {13, 16, 14, 15}};  // (++), (+-), (-+), (--)
-#pragma unroll
-  for (int a = 1; a <= 2; ++a) {
-    const R A = p[dg[a - 1][0]] + p[dg[a - 1][1]];  // sx = +1
-    const R B = p[dg[a - 1][2]] + p[dg[a - 1][3]];  // sx = -1
-    const R C = p[dg[a - 1][0]] - p[dg[a - 1][1]];
-    const R D = p[dg[a - 1][2]] - p[dg[a - 1][3]];
-    const R sum = A + B, xs = A - B, ys = C + D, xys = C - D;
-    m0 += sum;
-    m1 = madd(m1, xs, a);
-    m2 = madd(m2, ys, a);
-    m3 = madd(m3, sum, a * a);
-    m4 = madd(m4, xys, a * a);
-    m5 = madd(m5, sum, a * a);
-    m6 = madd(m6, xs, 2 * a * a * a);
-    m7 = madd(m7, ys, 2 * a * a * a);
-  }
-  M[0] = m0; M[1] = m1; M[2] = m2; M[3] = m3; M[4] = m4; M[5] = m5; M[6] = m6; M[7] = m7;
 }
 
 // 2^(j/32), j = 0..31; kernels copy it to shared memory (lanes index it freely).
@@ -150,51 +102,135 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   return q * sc;
 }
 
-// exp(-s) for the 21 velocities in FP32 (CUDA expf).
-__device__ __forceinline__ void exp_family32(const float l[NM], float p[Q]) {
-  float s[Q];
-  exponents<float>(l, s);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) p[i] = expf(-s[i]);
-}
+// Packed lower triangle of the 8x8 Jacobian: entry (a, b), b <= a.
+__host__ __device__ constexpr int tri(int a, int b) { return a * (a + 1) / 2 + b; }
 
-// Jacobi-scaled Cholesky factor of the Jacobian sum_i p_i P P^T, FP32.
-struct Fact32 {
-  float d[NM];       // scaling 1/sqrt(H_kk)
-  float L[NM][NM];   // lower factor of D H D
+// FP32 pass: F = sum p, G = sum p P and H = sum p P P^T at the visited
+// multipliers, accumulated velocity by velocity (compile-time monomials).
+struct PassGH32 {
+  float Fs, Gs[NM], Hs[36];
+  __device__ __forceinline__ PassGH32() {
+    Fs = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) Gs[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 36; ++k) Hs[k] = 0.0f;
+  }
+  template <int I>
+  __device__ __forceinline__ void point(float p) {
+    Fs += p;
+#pragma unroll
+    for (int a = 0; a < NM; ++a) {
+      Gs[a] = madd(Gs[a], p, PM(a, I));
+#pragma unroll
+      for (int b = 0; b <= a; ++b) Hs[tri(a, b)] = madd(Hs[tri(a, b)], p, PM(a, I) * PM(b, I));
+    }
+  }
+  __device__ __forceinline__ void rest(float s) { point<0>(expf(-s)); }
+  template <int A, int AX, int IP, int IM>
+  __device__ __forceinline__ void pair(float sp, float sm) { point<IP>(expf(-sp)); point<IM>(expf(-sm)); }
+  template <int A, int IPP, int IMP, int IMM, int IPM>
+  __device__ __forceinline__ void quad(float spp, float smp, float smm, float spm) {
+    point<IPP>(expf(-spp)); point<IMP>(expf(-smp)); point<IMM>(expf(-smm)); point<IPM>(expf(-spm));
+  }
+  __device__ __forceinline__ float F() const { return Fs; }
+  __device__ __forceinline__ void scale(float z) {
+    Fs *= z;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) Gs[k] *= z;
+#pragma unroll
+    for (int k = 0; k < 36; ++k) Hs[k] *= z;
+  }
+  __device__ __forceinline__ void assemble(float G[NM], float H[36]) const {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) G[k] = Gs[k];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) H[k] = Hs[k];
+  }
 };
 
-__device__ __forceinline__ bool factor32(const float p[Q], Fact32& fc) {
-  float H[NM][NM];
+// FP64 pass: the constraint sums M = sum p P with p = exp(-s) in FP64, each p
+// also written to the caller's shared column (p_i at col[i * stride]).
+struct PassG64 {
+  double M[NM];
+  const double* tab;
+  double* col;
+  int stride;
+  __device__ __forceinline__ PassG64(const double* t, double* c, int s) : tab(t), col(c), stride(s) {
 #pragma unroll
-  for (int a = 0; a < NM; ++a)
-#pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      float s = 0.0f;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) s = madd(s, p[i], PM(a, i) * PM(b, i));
-      H[a][b] = s;
+    for (int k = 0; k < NM; ++k) M[k] = 0.0;
+  }
+  __device__ __forceinline__ void rest(double s) {
+    const double p = exp_neg(s, tab);
+    col[0] = p;
+    M[0] += p;
+  }
+  template <int A, int AX, int IP, int IM>
+  __device__ __forceinline__ void pair(double sp, double sm) {
+    const double pp = exp_neg(sp, tab), pm = exp_neg(sm, tab);
+    col[IP * stride] = pp;
+    col[IM * stride] = pm;
+    const double S = pp + pm, D = pp - pm;
+    M[0] += S;
+    if (AX == 0) {
+      M[1] = madd(M[1], D, A);
+      M[3] = madd(M[3], S, A * A);
+      M[6] = madd(M[6], D, A * A * A);
+    } else {
+      M[2] = madd(M[2], D, A);
+      M[5] = madd(M[5], S, A * A);
+      M[7] = madd(M[7], D, A * A * A);
     }
+  }
+  template <int A, int IPP, int IMP, int IMM, int IPM>
+  __device__ __forceinline__ void quad(double spp, double smp, double smm, double spm) {
+    const double ppp = exp_neg(spp, tab), pmp = exp_neg(smp, tab);
+    const double pmm = exp_neg(smm, tab), ppm = exp_neg(spm, tab);
+    col[IPP * stride] = ppp;
+    col[IMP * stride] = pmp;
+    col[IMM * stride] = pmm;
+    col[IPM * stride] = ppm;
+    const double Ap = ppp + ppm, Bm = pmp + pmm;  // sx = +1, sx = -1
+    const double Cp = ppp - ppm, Dm = pmp - pmm;
+    const double sum = Ap + Bm, xs = Ap - Bm, ys = Cp + Dm, xys = Cp - Dm;
+    M[0] += sum;
+    M[1] = madd(M[1], xs, A);
+    M[2] = madd(M[2], ys, A);
+    M[3] = madd(M[3], sum, A * A);
+    M[4] = madd(M[4], xys, A * A);
+    M[5] = madd(M[5], sum, A * A);
+    M[6] = madd(M[6], xs, 2 * A * A * A);
+    M[7] = madd(M[7], ys, 2 * A * A * A);
+  }
+};
+
+// Jacobi-scaled Cholesky factor of the Jacobian, FP32.
+struct Fact32 {
+  float d[NM];    // scaling 1/sqrt(H_kk)
+  float L[36];    // packed lower factor of D H D
+};
+
+__device__ __forceinline__ bool factor32(const float H[36], Fact32& fc) {
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < NM; ++k) {
-    ok = ok && (H[k][k] > 0.0f);
-    fc.d[k] = rsqrtf(fmaxf(H[k][k], 1e-30f));
+    ok = ok && (H[tri(k, k)] > 0.0f);
+    fc.d[k] = rsqrtf(fmaxf(H[tri(k, k)], 1e-30f));
   }
 #pragma unroll
   for (int j = 0; j < NM; ++j) {
-    float dj = H[j][j] * fc.d[j] * fc.d[j];
+    float dj = H[tri(j, j)] * fc.d[j] * fc.d[j];
 #pragma unroll
-    for (int k = 0; k < j; ++k) dj = fmaf(-fc.L[j][k], fc.L[j][k], dj);
+    for (int k = 0; k < j; ++k) dj = fmaf(-fc.L[tri(j, k)], fc.L[tri(j, k)], dj);
     ok = ok && (dj > 0.0f);
     const float il = rsqrtf(fmaxf(dj, 1e-30f));
-    fc.L[j][j] = dj * il;
+    fc.L[tri(j, j)] = dj * il;
 #pragma unroll
     for (int i = j + 1; i < NM; ++i) {
-      float s = H[i][j] * fc.d[i] * fc.d[j];
+      float s = H[tri(i, j)] * fc.d[i] * fc.d[j];
 #pragma unroll
-      for (int k = 0; k < j; ++k) s = fmaf(-fc.L[i][k], fc.L[j][k], s);
-      fc.L[i][j] = s * il;
+      for (int k = 0; k < j; ++k) s = fmaf(-fc.L[tri(i, k)], fc.L[tri(j, k)], s);
+      fc.L[tri(i, j)] = s * il;
     }
   }
   return ok;
@@ -207,15 +243,15 @@ __device__ __forceinline__ void solve32(const Fact32& fc, const float g[NM], flo
   for (int i = 0; i < NM; ++i) {
     float s = g[i] * fc.d[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) s = fmaf(-fc.L[i][k], y[k], s);
-    y[i] = s / fc.L[i][i];
+    for (int k = 0; k < i; ++k) s = fmaf(-fc.L[tri(i, k)], y[k], s);
+    y[i] = s / fc.L[tri(i, i)];
   }
 #pragma unroll
   for (int i = NM - 1; i >= 0; --i) {
     float s = y[i];
 #pragma unroll
-    for (int k = i + 1; k < NM; ++k) s = fmaf(-fc.L[k][i], y[k], s);
-    y[i] = s / fc.L[i][i];
+    for (int k = i + 1; k < NM; ++k) s = fmaf(-fc.L[tri(k, i)], y[k], s);
+    y[i] = s / fc.L[tri(i, i)];
   }
 #pragma unroll
   for (int i = 0; i < NM; ++i) dl[i] = y[i] * fc.d[i];
@@ -255,15 +291,14 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
     m[3] = fmaf(ubx, ubx, T); m[4] = ubx * uby; m[5] = fmaf(uby, uby, T);
     m[6] = ubx * fmaf(4.0f, T, u2); m[7] = uby * fmaf(4.0f, T, u2);
   }
-  float p[Q];
+  PassGH32 ps;
   if (warm) {
-    exp_family32(lam, p);
-    float Z = 0.0f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) Z += p[i];
-    warm = isfinite(Z) && Z > 0.0f;
+    visit_groups<float>(lam, ps);
+    warm = isfinite(ps.F()) && ps.F() > 0.0f;
   }
   if (!warm) {
+    // Maxwellian multipliers; lambda_0 from the normalisation sum p = 1 (the
+    // pass at lambda_0 = 0 gives Z = F, and all its sums scale by 1/Z)
     const float iT = 1.0f / T;
 #pragma unroll
     for (int k = 0; k < NM; ++k) lam[k] = 0.0f;
@@ -271,29 +306,24 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
     lam[2] = -uby * iT;
     lam[3] = 0.5f * iT;
     lam[5] = 0.5f * iT;
-    exp_family32(lam, p);
-    float Z = 0.0f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) Z += p[i];
-    const float l0 = logf(Z);
-    const float iz = 1.0f / Z;
-    lam[0] = l0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) p[i] *= iz;
+    ps = PassGH32();
+    visit_groups<float>(lam, ps);
+    const float iz = 1.0f / ps.F();
+    lam[0] = logf(ps.F());
+    ps.scale(iz);
   }
-  auto dual = [&](const float* l, const float* pp) {
-    float F = 0.0f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) F += pp[i];
+  auto dual = [&](const float* l, float F) {
 #pragma unroll
     for (int k = 0; k < NM; ++k) F = fmaf(l[k], m[k], F);
     return F;
   };
-  float F = dual(lam, p);
+  float Fd = dual(lam, ps.F());
+  float H[36];
   int it = 0;
+  bool factored = false;
   for (; it < maxit; ++it) {
     float G[NM];
-    moments8<float>(p, G);
+    ps.assemble(G, H);
     float gmax = 0.0f;
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
@@ -301,69 +331,83 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
       gmax = fmaxf(gmax, fabsf(G[k]));
     }
     if (!isfinite(gmax)) return NEWTON_SINGULAR;
+    if (!factor32(H, fc)) return NEWTON_SINGULAR;
+    factored = true;
     if (gmax <= 2e-7f) break;
-    if (!factor32(p, fc)) return NEWTON_SINGULAR;
     float dl[NM];
     solve32(fc, G, dl);
     float gd = 0.0f;
 #pragma unroll
     for (int k = 0; k < NM; ++k) gd = fmaf(G[k], dl[k], gd);
-    if (!(gd > 1e-14f)) break;  // no further progress is measurable in FP32
-    float t = 1.0f, lc[NM], pc[Q], Fc = 0.0f;
+    if (!(gd > 0.0f)) break;
+    if (gd <= 2e-6f * fmaxf(1.0f, fabsf(Fd))) {
+      // The predicted decrease gd/2 of the dual lies below its FP32 resolution:
+      // a line search would only compare rounding noise. This close to the root
+      // the full Newton step is safe; take it and leave the rest to the FP64
+      // refinement (the factor of the previous multipliers serves it).
+#pragma unroll
+      for (int k = 0; k < NM; ++k) lam[k] += dl[k];
+      ++it;
+      break;
+    }
+    float t = 1.0f, lc[NM];
     bool acc = false;
-    for (int ls = 0; ls < 24; ++ls) {
+    for (int ls = 0; ls < 12; ++ls) {
 #pragma unroll
       for (int k = 0; k < NM; ++k) lc[k] = fmaf(t, dl[k], lam[k]);
-      exp_family32(lc, pc);
-      Fc = dual(lc, pc);
-      if (isfinite(Fc) && Fc <= F - 1e-4f * t * gd + 4e-7f * fabsf(F)) {
+      PassGH32 pc;
+      visit_groups<float>(lc, pc);
+      const float Fc = dual(lc, pc.F());
+      if (isfinite(Fc) && Fc <= Fd - 1e-4f * t * gd + 4e-7f * fabsf(Fd)) {
         acc = true;
+        ps = pc;
+        Fd = Fc;
         break;
       }
       t *= 0.5f;
     }
+    factored = false;
     if (!acc) break;
 #pragma unroll
     for (int k = 0; k < NM; ++k) lam[k] = lc[k];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) p[i] = pc[i];
-    F = Fc;
   }
   *iters = it;
-  return factor32(p, fc) ? NEWTON_OK : NEWTON_SINGULAR;
+  if (!factored) {
+    float G[NM];
+    ps.assemble(G, H);
+    if (!factor32(H, fc)) return NEWTON_SINGULAR;
+  }
+  return NEWTON_OK;
 }
 
 // FP64 refinement: lambda <- lambda + H32^-1 G64(lambda) until max|G|/rho <= tol.
-// On NEWTON_OK, p holds exp(-s) in FP64 at the returned lambda.
+// On NEWTON_OK the FP64 equilibrium per unit density at the returned lambda
+// is in col[i * stride] (a shared-memory column of the calling thread).
 static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T, double tol,
                                                int maxr, const float lam32[NM], const Fact32& fc,
-                                               const double* tab, double lam[NM], double p[Q],
-                                               int* evals) {
+                                               const double* tab, double* col, int stride,
+                                               double lam[NM], int* evals) {
   double m[NM];
   targets(ubx, uby, T, m);
 #pragma unroll
   for (int k = 0; k < NM; ++k) lam[k] = (double)lam32[k];
   *evals = 0;
   for (int r = 0;; ++r) {
-    double s[Q];
-    exponents<double>(lam, s);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) p[i] = exp_neg(s[i], tab);
-    double G[NM];
-    moments8<double>(p, G);
+    PassG64 ps(tab, col, stride);
+    visit_groups<double>(lam, ps);
     ++*evals;
     double gmax = 0.0;
+    float g32[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
-      G[k] -= m[k];
-      gmax = fmax(gmax, fabs(G[k]));
+      const double G = ps.M[k] - m[k];
+      gmax = fmax(gmax, fabs(G));
+      g32[k] = (float)G;
     }
     if (!isfinite(gmax)) return NEWTON_SINGULAR;
     if (gmax <= tol) return NEWTON_OK;
     if (r >= maxr) return NEWTON_MAXIT;
-    float g32[NM], dl[NM];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) g32[k] = (float)G[k];
+    float dl[NM];
     solve32(fc, g32, dl);
 #pragma unroll
     for (int k = 0; k < NM; ++k) lam[k] += (double)dl[k];
@@ -377,11 +421,12 @@ struct SolveCount {
 
 // Equilibrium of the FP32 form: FP32 Newton (from the warm start if given,
 // else from the Maxwellian; again from the Maxwellian if the warm start
-// fails), FP64 refinement, full FP64 Newton as the last fallback. p receives
-// exp(-(1 + lambda . P)) in FP64.
+// fails), FP64 refinement, full FP64 Newton as the last fallback. The FP64
+// equilibrium per unit density lands in col[i * stride].
 __device__ __forceinline__ int equilibrium_mixed(double ubx, double uby, double T, double tol,
                                                  int maxit, const double* tab, const float* warm,
-                                                 double lam[NM], double p[Q], SolveCount* cnt) {
+                                                 double* col, int stride, double lam[NM],
+                                                 SolveCount* cnt) {
   if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
   float lam32[NM];
   Fact32 fc;
@@ -398,14 +443,17 @@ __device__ __forceinline__ int equilibrium_mixed(double ubx, double uby, double 
     cnt->fp32_iters += it32;
   }
   if (st == NEWTON_OK) {
-    st = refine_fp64(ubx, uby, T, tol, 6, lam32, fc, tab, lam, p, &ev);
+    st = refine_fp64(ubx, uby, T, tol, 6, lam32, fc, tab, col, stride, lam, &ev);
     cnt->fp64_evals += ev;
   }
   if (st != NEWTON_OK) {
+    double p[Q];
     int it = 0;
     st = newton_fp64(ubx, uby, T, tol, maxit, lam, p, &it, &ev);
     cnt->fp64_iters += it;
     cnt->fp64_evals += ev;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) col[i * stride] = p[i];
   }
   return st;
 }

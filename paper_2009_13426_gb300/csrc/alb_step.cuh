@@ -1,0 +1,338 @@
+// Per-node update of the adaptive D2Q21 LBM step (Sec. IV.A.3), shared by the
+// single-flow and the batched kernels.
+//
+// One thread updates one node. Its pulled populations (42, precision P) and
+// the 21 FP64 equilibrium values per unit density of its latest equilibrium
+// solve sit in two columns of the block's dynamic shared memory, with the
+// block size as stride.
+#pragma once
+
+#include <type_traits>
+
+#include "alb_internal.h"
+#include "alb_mixed.cuh"
+
+namespace alb {
+
+constexpr int BLOCK = 128;
+
+template <typename P, int B = BLOCK>
+constexpr size_t smem_bytes() {
+  return (size_t)NPLANES * B * sizeof(P) + (size_t)Q * B * sizeof(double);
+}
+
+// Shared columns of this thread: populations (P) and equilibrium (double),
+// both with stride B (the block size).
+template <typename P, int B>
+struct Columns {
+  P* pop;
+  double* eq;
+  __device__ __forceinline__ Columns(unsigned char* smem) {
+    pop = reinterpret_cast<P*>(smem) + threadIdx.x;
+    eq = reinterpret_cast<double*>(smem + (size_t)NPLANES * B * sizeof(P)) + threadIdx.x;
+  }
+};
+
+// Equilibrium of one node in the storage precision P: the full FP64 Newton for
+// the FP64 plain path, the mixed FP32/FP64 solver for the FP32 form. The
+// equilibrium per unit density lands in eq[i * B].
+template <typename P, int B = BLOCK>
+__device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, double uby,
+                                                double T, const double* tab, const float* warm,
+                                                double* eq, double lam[NM], SolveCount* cnt) {
+  if constexpr (std::is_same<P, float>::value) {
+    return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, eq, B, lam, cnt);
+  } else {
+    int it = 0, ev = 0;
+    double p[Q];
+    const int st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev);
+    cnt->fp64_iters += it;
+    cnt->fp64_evals += ev;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) eq[i * B] = p[i];
+    return st;
+  }
+}
+
+// Moment accumulation: plain in FP64; Neumaier-compensated in FP32.
+template <typename P>
+struct Acc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double val() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    if (fabsf(s) >= fabsf(v))
+      c += (s - t) + v;
+    else
+      c += (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double val() const { return (double)(s + c); }
+  __device__ __forceinline__ float valf() const { return s + c; }
+};
+
+template <typename P>
+struct StepArgs {
+  const P* pop_in;
+  P* pop_out;
+  const P* mom_in;
+  P* mom_out;
+  const uint8_t* lat_in;
+  const uint8_t* nxt_in;
+  uint8_t* lat_out;
+  uint8_t* nxt_out;
+  const float* lam_in;  // FP32 form: multipliers of the previous step (8 planes)
+  float* lam_out;
+  size_t ps;
+  Params prm;
+  unsigned long long* ctr;
+};
+
+// Multipliers stored for node k (8 planes), moved into the frame of lattice
+// (Ux, Uy) from the lattice code they were computed in.
+__device__ __forceinline__ void load_warm(const float* lam, size_t ps, size_t k, int code_from,
+                                          int Ux, int Uy, float w[NM]) {
+  float l[NM];
+#pragma unroll
+  for (int j = 0; j < NM; ++j) l[j] = lam[j * ps + k];
+  const int dx = lat_ux(code_from) - Ux, dy = lat_uy(code_from) - Uy;
+  if (dx == 0 && dy == 0) {
+#pragma unroll
+    for (int j = 0; j < NM; ++j) w[j] = l[j];
+  } else {
+    shift_multipliers(l, (float)dx, (float)dy, w);
+  }
+}
+
+// Grad rebuild of a missing pull (Sec. III.B.2, IV.A.3): the post-collision
+// population of velocity i = (cx, cy) in the receiver's lattice (Upx, Upy),
+// built from the sender's moments at (sx, sy) (possibly a ghost), their
+// central differences and the sender's relaxation time:
+// h* = h^eq (1 + (1 - 1/tau) phi_h). Uses the thread's equilibrium column as
+// scratch. Returns 1 if the root finder failed and the Maxwellian-guess
+// fallback was used.
+template <typename P, int B>
+__device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
+                                         int i, int cx, int cy, int Upx, int Upy, int sx, int sy,
+                                         double* fi, double* gi, const double* tab, double* eq,
+                                         const float* lam_in, const uint8_t* lat_in,
+                                         SolveCount* cnt) {
+  bool gh = false;
+  const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
+  const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
+  const int xp = resolve(sx + 1, pr.nx, pr.bcx, &gh);
+  const int xm = resolve(sx - 1, pr.nx, pr.bcx, &gh);
+  const int yp = resolve(sy + 1, pr.ny, pr.bcy, &gh);
+  const int ym = resolve(sy - 1, pr.ny, pr.bcy, &gh);
+  const size_t nx = (size_t)pr.nx;
+  const size_t ks = ry * nx + rx;
+  const size_t kxp = ry * nx + xp, kxm = ry * nx + xm, kyp = yp * nx + rx, kym = ym * nx + rx;
+  const P* mr = mom;
+  const P* mux = mom + ps;
+  const P* muy = mom + 2 * ps;
+  const P* mT = mom + 3 * ps;
+  const double rho = (double)mr[ks], ux = (double)mux[ks], uy = (double)muy[ks],
+               T = (double)mT[ks];
+  double du[2][2], dT[2];
+  du[0][0] = 0.5 * ((double)mux[kxp] - (double)mux[kxm]);
+  du[1][0] = 0.5 * ((double)mux[kyp] - (double)mux[kym]);
+  du[0][1] = 0.5 * ((double)muy[kxp] - (double)muy[kxm]);
+  du[1][1] = 0.5 * ((double)muy[kyp] - (double)muy[kym]);
+  dT[0] = 0.5 * ((double)mT[kxp] - (double)mT[kxm]);
+  dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
+  const double ubx = ux - Upx, uby = uy - Upy;
+  double lam[NM];
+  float wbuf[NM];
+  const float* warm = nullptr;
+  if constexpr (std::is_same<P, float>::value) {
+    load_warm(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
+    warm = wbuf;
+  }
+  const int st = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, eq, lam, cnt)
+                             : NEWTON_UNREALIZABLE;
+  const double gfac = (2.0 * pr.cv - 2.0) * T;
+  if (st != NEWTON_OK) {
+    if (T > 0.0) {
+      maxwellian_guess(ubx, uby, T, lam);
+      *fi = rho * exp_family_one(lam, cx, cy);
+    } else {
+      *fi = 0.0;
+    }
+    *gi = gfac * (*fi);
+    return 1;
+  }
+  const double tau = 0.5 + pr.nu / T;
+  const double omega = 1.0 - 1.0 / tau;
+  const double feq = rho * eq[i * B];
+  const double cbx = (double)(cx + Upx) - ux;
+  const double cby = (double)(cy + Upy) - uy;
+  double phf, phg;
+  grad_phi(pr, rho, T, cbx, cby, du, dT, &phf, &phg);
+  *fi = feq * (1.0 + omega * phf);
+  *gi = gfac * feq * (1.0 + omega * phg);
+  return 0;
+}
+
+// Moments, next shift, equilibrium and BGK of one node whose 42 pre-collision
+// populations sit in its shared column, then store.
+template <typename P, int B>
+__device__ __forceinline__ void collide_store(const Params& pr, const Columns<P, B>& cl, int code,
+                                              size_t k, size_t ps, P* __restrict__ pop_out,
+                                              P* __restrict__ mom_out, uint8_t* lat_out,
+                                              uint8_t* nxt_out, const double* tab,
+                                              const float* warm, float* lam_out,
+                                              SolveCount* cnt, unsigned* n_fail) {
+  const P* st = cl.pop;
+  const int Ux = lat_ux(code), Uy = lat_uy(code);
+  Acc<P> ar, ajx, ajy, ae;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const P f = st[i * B];
+    const P g = st[(Q + i) * B];
+    ar.add(f);
+    if (XI_X(i) != 0) ajx.add(XI_X(i) == 1 ? f : XI_X(i) == -1 ? -f : (P)XI_X(i) * f);
+    if (XI_Y(i) != 0) ajy.add(XI_Y(i) == 1 ? f : XI_Y(i) == -1 ? -f : (P)XI_Y(i) * f);
+    const int c2 = XI_X(i) * XI_X(i) + XI_Y(i) * XI_Y(i);
+    if (c2 != 0) ae.add(c2 == 1 ? f : (P)c2 * f);
+    ae.add(g);
+  }
+  // Moments (Eq. polyTemp). The velocity and temperature that define the
+  // equilibrium's targets are formed in FP64 from the (FP32 or FP64) sums, so
+  // that the collision conserves the sums to their own precision; the next
+  // lattice (Eq. criterion) is chosen from u = (rho u) / rho in FP64.
+  const double rho = ar.val();
+  const double ubx = ajx.val() / rho, uby = ajy.val() / rho;
+  const double T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
+  const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
+  const int code2 = lat_code(select_shift_thr(ux, pr), select_shift_thr(uy, pr));
+
+  double lam[NM];
+  const int ns = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, cl.eq, lam, cnt)
+                             : NEWTON_UNREALIZABLE;
+  if constexpr (std::is_same<P, float>::value) {
+    // multipliers for the next step's warm start (lattice `code`)
+    if (ns == NEWTON_OK) {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = (float)lam[j];
+    } else if (warm) {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = warm[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = j == 3 || j == 5 ? 0.5f : 0.0f;
+    }
+  }
+  if (ns == NEWTON_OK) {
+    // f^eq = rho p, g^eq = (2 Cv - D) T f^eq and tau = 1/2 + nu/T in the
+    // population precision (in the FP32 form from the FP64 equilibrium)
+    const P Tp = (P)T;
+    const P gp = ((P)2 * (P)pr.cv - (P)2) * Tp;
+    P tau = (P)0.5 + (P)pr.nu / Tp;
+    const P rp = (P)rho;
+    if (pr.sensor) {
+      P eps = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const P fe = (P)cl.eq[i * B] * rp;
+        eps += fabs(st[i * B] - fe) / fe;
+      }
+      eps /= (P)Q;
+      tau *= sensor_alpha<P>(pr, eps);
+    }
+    const P om = (P)1 / tau;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const P fe = (P)cl.eq[i * B] * rp;
+      const P ge = gp * fe;
+      const P f = st[i * B];
+      const P g = st[(Q + i) * B];
+      pop_out[i * ps + k] = fma(om, fe - f, f);
+      pop_out[(Q + i) * ps + k] = fma(om, ge - g, g);
+    }
+  } else {
+    *n_fail += 1;
+#pragma unroll
+    for (int i = 0; i < NPLANES; ++i) pop_out[i * ps + k] = st[i * B];
+  }
+  mom_out[k] = (P)rho;
+  mom_out[ps + k] = (P)ux;
+  mom_out[2 * ps + k] = (P)uy;
+  mom_out[3 * ps + k] = (P)T;
+  lat_out[k] = (uint8_t)code;
+  nxt_out[k] = (uint8_t)code2;
+}
+
+// Counts of one node update, added to the flow's counters warp by warp.
+struct NodeCount {
+  SolveCount solve;
+  unsigned rec = 0, rec_fail = 0, fail = 0, calls = 0;
+};
+
+__device__ __forceinline__ void flush_counts(unsigned long long* ctr, const NodeCount& c) {
+  warp_count(ctr + CTR_NEWTON_ITERS, c.solve.fp64_iters);
+  warp_count(ctr + CTR_FP64_EVALS, c.solve.fp64_evals);
+  warp_count(ctr + CTR_FP32_ITERS, c.solve.fp32_iters);
+  warp_count(ctr + CTR_NEWTON_CALLS, c.calls);
+  warp_count(ctr + CTR_NEWTON_FAIL, c.fail);
+  warp_count(ctr + CTR_REC, c.rec);
+  warp_count(ctr + CTR_REC_FAIL, c.rec_fail);
+}
+
+// One time step of node (x, y) of a flow (Sec. IV.A.3): pull in the lattice
+// selected at the previous step, rebuild the missing pulls, collide, store.
+template <typename P, int B>
+__device__ __forceinline__ void node_step(const StepArgs<P>& a, int x, int y,
+                                          const Columns<P, B>& cl, const double* s_tab,
+                                          NodeCount& nc) {
+  const Params& pr = a.prm;
+  const size_t k = (size_t)y * pr.nx + x;
+  const size_t ps = a.ps;
+  const int code = a.nxt_in[k];
+  const int Upx = lat_ux(code), Upy = lat_uy(code);
+  // pull every population whose sender lives in the same lattice; record the
+  // missing ones (bit i) and rebuild them afterwards from a single call site
+  unsigned missing = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int sx = x - XI_X(i) - Upx;
+    const int sy = y - XI_Y(i) - Upy;
+    bool gh = false;
+    const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
+    const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
+    const size_t ks = (size_t)ry * pr.nx + rx;
+    if (!gh && a.lat_in[ks] == code) {
+      cl.pop[i * B] = a.pop_in[i * ps + ks];
+      cl.pop[(Q + i) * B] = a.pop_in[(Q + i) * ps + ks];
+    } else {
+      missing |= 1u << i;
+    }
+  }
+  while (missing) {
+    const int i = __ffs(missing) - 1;
+    missing &= missing - 1;
+    const int cx = XI_X(i), cy = XI_Y(i);
+    double fd, gd;
+    nc.rec += 1;
+    nc.rec_fail += rebuild_pull<P, B>(pr, a.mom_in, ps, i, cx, cy, Upx, Upy, x - cx - Upx,
+                                      y - cy - Upy, &fd, &gd, s_tab, cl.eq, a.lam_in, a.lat_in,
+                                      &nc.solve);
+    cl.pop[i * B] = (P)fd;
+    cl.pop[(Q + i) * B] = (P)gd;
+  }
+  float wbuf[NM];
+  const float* warm = nullptr;
+  if constexpr (std::is_same<P, float>::value) {
+    load_warm(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
+    warm = wbuf;
+  }
+  collide_store<P, B>(pr, cl, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,
+                      warm, a.lam_out, &nc.solve, &nc.fail);
+  nc.calls += 1 + nc.rec;
+}
+
+}  // namespace alb

@@ -331,3 +331,26 @@ def test_oracle_sod_tube_against_exact_solution():
     assert abs(ux[sl].mean() - us) < 0.02 * us
     # the post-shock region lives in lattice U_x = 1 (u* > 0.5)
     assert set(np.unique(s.shifts()[0])) == {0, 1}
+
+
+def test_replayed_lattice_decisions_reproduce_the_free_run():
+    """ora_step_forced with the decisions the criterion itself takes gives the
+    same state bit for bit; other decisions change the state; shifts beyond
+    u_max are refused."""
+    n = 24
+    fields = flows.isentropic_vortex(n, n, radius=4.0, mach=1.0)
+    a = O.Simulation(O.make_config(n, n))
+    b = O.Simulation(O.make_config(n, n))
+    c = O.Simulation(O.make_config(n, n))
+    for s in (a, b, c):
+        assert s.init(*fields) == O.OK
+    for _ in range(6):
+        assert a.step(1) == O.OK
+        ux, uy = a.shifts()
+        assert b.step_forced(ux, uy) == O.OK
+        assert c.step_forced(*c.shifts()) == O.OK  # never change lattice
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x, y)
+    assert not np.array_equal(a.moments()[1], c.moments()[1])
+    bad = np.full((n, n), 5, np.int8)
+    assert b.step_forced(bad, bad) != O.OK
