@@ -223,6 +223,190 @@ int alb_select_shift(const double* rho, const double* rhou, int n, double n0, in
 /* D2Q21 velocity table used by every entry point (host memory, 21 each). */
 int alb_velocities(int* xi_x, int* xi_y);
 
+/* ------------------------------------------------------------------------
+ * Batched flows. Many independent flows, each with its own grid size and
+ * parameters, advance together: one persistent kernel launch per time step
+ * and precision walks a table of work items (a tile of one flow each), and
+ * two steps are replayed as one CUDA graph. A node's update is the same code
+ * as in alb_step and reads only its own flow's state, so a flow's results
+ * do not depend on the batch it runs in, on the tile shape or on the kernel
+ * variant. The paper has no counterpart: it describes one flow at a time. */
+typedef struct alb_batch alb_batch; /* opaque */
+
+/* Launch shape of the batched kernel for one precision.
+ *   variant        compiled kernel variant: index into alb_batch_variants
+ *                  (block size and minimum resident blocks per SM, which
+ *                  bounds the registers per thread).
+ *   tile_w[3]      tile width in nodes for flows with nx < 128, with
+ *                  nx < 512, and wider; the tile height is block / tile_w.
+ *                  Powers of two in [8, block].
+ *   dynamic        1: blocks fetch work items from an atomic counter;
+ *                  0: block b takes items b, b + grid, b + 2 grid, ...
+ *   blocks_per_sm  resident blocks per SM of the persistent grid (0: the
+ *                  occupancy maximum; larger values are capped by it). */
+typedef struct {
+  int variant;
+  int tile_w[3];
+  int dynamic;
+  int blocks_per_sm;
+} alb_batch_tuning;
+
+/* Compiled variants of a precision: *count (at most 8) and, if non-NULL,
+ * block[v] and min_blocks[v] for each. */
+int alb_batch_variants(int precision, int* count, int* block, int* min_blocks);
+
+/* Create nflows (>= 1) flows from cfgs[0..nflows-1] (any mix of sizes,
+ * parameters and precisions; each cfg's stream is ignored). All work runs on
+ * `stream` (cudaStream_t; NULL: the batch creates one; not the legacy
+ * default stream, which cannot be captured). Default launch shape: variant
+ * 0, tiles of 64 / 128 / 128 nodes (at most the block), dynamic items. */
+int alb_batch_create(const alb_config* cfgs, int nflows, void* stream, alb_batch** out);
+
+/* Handle of flow i (0 <= i < nflows), owned by the batch: use it with
+ * alb_init (required before the first alb_batch_step), alb_moments,
+ * alb_shifts, alb_totals, alb_stats_get, alb_sync and alb_step (which steps
+ * that flow alone); alb_destroy refuses it (ALB_EINVAL). */
+int alb_batch_flow(alb_batch* b, int i, alb_handle** out);
+
+/* Enqueue nsteps time steps of every flow (all must be initialised) on the
+ * batch's stream: nsteps / 2 replays of a two-step CUDA graph, then one more
+ * step if nsteps is odd. Returns after enqueueing. The first call after
+ * creation or a tuning change captures the graph. */
+int alb_batch_step(alb_batch* b, int nsteps);
+
+/* Wait for the batch's stream (alb_sync on every flow; timeout_ms as there). */
+int alb_batch_sync(alb_batch* b, int timeout_ms);
+
+/* Autotuner: for each precision present, time the kernel variants, then the
+ * tile width of each size class of flows present (timing that class's items
+ * alone), then static against dynamic work distribution, with `trials`
+ * timed launches (>= 1) per candidate, and keep the fastest. Every timed
+ * launch reads the current state and writes only the spare buffers, and the
+ * flows' counters are restored, so the flows do not advance. Flows must be
+ * initialised. Synchronises the stream. */
+int alb_batch_tune(alb_batch* b, int trials);
+
+/* Read or set the launch shape of one precision (set: ALB_EINVAL if the
+ * shape is invalid; synchronises the stream). */
+int alb_batch_get_tuning(alb_batch* b, int precision, alb_batch_tuning* t);
+int alb_batch_set_tuning(alb_batch* b, int precision, const alb_batch_tuning* t);
+
+/* Free the batch and all its flows (synchronises first). */
+int alb_batch_destroy(alb_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Serving loop. A server owns two threads and two streams. Requests (a
+ * flow configuration, its initial fields and a step count) queue as they
+ * are submitted. The admission thread takes the queued request of least
+ * estimated work (nodes x steps x the measured time of a node update of its
+ * precision) that fits the device-memory budget, while the resident flows
+ * hold fewer than 2 batch_nodes nodes, and creates and Grad-initialises its
+ * flow on its own stream, overlapping the stepping. The worker thread
+ * advances the resident flows in chunks of steps with the batched kernel of
+ * alb_batch_step (least remaining work first, up to batch_nodes nodes per
+ * chunk; each flow for exactly its remaining steps), so requests that
+ * arrive while others run join at the next chunk. A finished flow's moments
+ * go to host memory and its device memory is freed. Results are identical to
+ * those of the same request run alone through alb_step. Under sustained
+ * overload, requests of large work wait for as long as smaller ones keep
+ * arriving. The paper has no counterpart: this is a service of the library.
+ */
+typedef struct alb_server alb_server; /* opaque */
+
+/* Server settings.
+ *   hbm_fraction  admission budget as a fraction of the device's total
+ *                 memory (0 < f <= 1; 0.8 by default), capped by the memory
+ *                 free at creation minus 1 GiB.
+ *   chunk_ms      target duration of a chunk of steps (> 0; 100 by
+ *                 default); the worker sizes chunks from the previous one.
+ *   max_chunk     most steps in one chunk (>= 1; 256 by default).
+ *   max_flows     most resident flows (0: no limit).
+ *   batch_nodes   nodes stepped per chunk at most (0: every resident flow
+ *                 steps in every chunk; 2^22 by default). Resident flows are
+ *                 ranked by remaining work (nodes x steps left x the measured
+ *                 time of a node update of their precision), least first,
+ *                 and taken in that order until their nodes reach
+ *                 batch_nodes (at least one flow per chunk).
+ *   tune          1: run alb_batch_tune's search once on the first chunk
+ *                 that holds flows of a precision (0 by default). */
+typedef struct {
+  double hbm_fraction;
+  double chunk_ms;
+  int max_chunk;
+  int max_flows;
+  long long batch_nodes;
+  int tune;
+} alb_server_config;
+
+/* Producer of a request's initial fields, called on the worker thread when
+ * the request is admitted: fill rho, rho ux, rho uy, rho E (host arrays of
+ * nx*ny doubles, x fastest) and return 0, or non-zero to fail the request. */
+typedef int (*alb_fill_fn)(void* user, double* rho, double* rhoux, double* rhouy, double* rhoE);
+
+/* A request. cfg: the flow (its stream is ignored). nsteps >= 0.
+ * Initial fields: either host arrays rho..rhoE (copied by alb_submit), or,
+ * with those NULL, fill(user, ...) at admission (user must stay valid until
+ * then). keep_result: 1 keeps the final moments in host memory until
+ * alb_poll collects them; 0 keeps only the status and times. */
+typedef struct {
+  alb_config cfg;
+  int nsteps;
+  const double* rho;
+  const double* rhoux;
+  const double* rhouy;
+  const double* rhoE;
+  alb_fill_fn fill;
+  void* user;
+  int keep_result;
+} alb_request;
+
+enum { ALB_QUEUED = 0, ALB_RUNNING = 1, ALB_DONE = 2, ALB_FAILED = 3 };
+
+/* Outcome of a request. The caller sets rho..rhoE to host arrays of nx*ny
+ * doubles to receive the final moments (NULL: not copied; ignored unless
+ * keep_result was 1). Times are seconds since the server's creation. */
+typedef struct {
+  double* rho;
+  double* rhoux;
+  double* rhouy;
+  double* rhoE;
+  int status;         /* ALB_OK, or the error that failed or flagged the request */
+  uint64_t steps;     /* steps taken */
+  alb_stats stats;    /* the flow's counters at completion */
+  double t_submit, t_admit, t_done;
+} alb_result;
+
+/* Aggregate counters of a server. */
+typedef struct {
+  uint64_t submitted, admitted, completed, failed;
+  uint64_t queued, running;
+  uint64_t node_updates;       /* node updates of all chunks so far */
+  uint64_t chunks, steps;      /* chunks run, and batched steps within them */
+  uint64_t resident_bytes;     /* device memory of the resident flows */
+  uint64_t budget_bytes;       /* admission budget */
+  double busy_seconds;         /* wall time spent running chunks */
+  double elapsed_seconds;      /* since creation */
+} alb_server_stats;
+
+/* Fill *c with the defaults above. */
+int alb_server_config_default(alb_server_config* c);
+/* Create a server on the current device (starts its worker thread). */
+int alb_server_create(const alb_server_config* c, alb_server** out);
+/* Queue a request; *id identifies it. ALB_EINVAL for a bad request,
+ * ALB_ENOMEM if the flow alone exceeds the budget (nothing queued). */
+int alb_submit(alb_server* s, const alb_request* r, uint64_t* id);
+/* Non-blocking state of request id (*state one of ALB_QUEUED .. ALB_FAILED).
+ * Once it is DONE or FAILED the call fills *res (if non-NULL) and forgets
+ * the request: a later poll of that id gives ALB_ENOTFOUND. */
+int alb_poll(alb_server* s, uint64_t id, int* state, alb_result* res);
+/* Block until no request is queued or running, at most timeout_ms (< 0: no
+ * limit); ALB_ETIMEDOUT otherwise. */
+int alb_server_drain(alb_server* s, int timeout_ms);
+int alb_server_stats_get(alb_server* s, alb_server_stats* out);
+/* Stop the worker after its current chunk and free everything; requests
+ * still queued or running are dropped. */
+int alb_server_destroy(alb_server* s);
+
 #ifdef __cplusplus
 }
 #endif

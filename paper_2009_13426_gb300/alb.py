@@ -61,6 +61,45 @@ class alb_stats(ctypes.Structure):
         "reconstruction_failures", "newton_calls", "fp64_evaluations", "fp32_iterations")]
 
 
+class alb_batch_tuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tile_w", ctypes.c_int * 3),
+                ("dynamic", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+
+class alb_server_config(ctypes.Structure):
+    _fields_ = [("hbm_fraction", ctypes.c_double), ("chunk_ms", ctypes.c_double),
+                ("max_chunk", ctypes.c_int), ("max_flows", ctypes.c_int),
+                ("batch_nodes", ctypes.c_longlong), ("tune", ctypes.c_int)]
+
+
+FILL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double))
+
+
+class alb_request(ctypes.Structure):
+    _fields_ = [("cfg", alb_config), ("nsteps", ctypes.c_int),
+                ("rho", ctypes.c_void_p), ("rhoux", ctypes.c_void_p), ("rhouy", ctypes.c_void_p),
+                ("rhoE", ctypes.c_void_p), ("fill", FILL_FN), ("user", ctypes.c_void_p),
+                ("keep_result", ctypes.c_int)]
+
+
+class alb_result(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_void_p), ("rhoux", ctypes.c_void_p), ("rhouy", ctypes.c_void_p),
+                ("rhoE", ctypes.c_void_p), ("status", ctypes.c_int), ("steps", ctypes.c_uint64),
+                ("stats", alb_stats), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class alb_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "admitted", "completed", "failed", "queued", "running", "node_updates",
+        "chunks", "steps", "resident_bytes", "budget_bytes")] + [
+        ("busy_seconds", ctypes.c_double), ("elapsed_seconds", ctypes.c_double)]
+
+
+ALB_QUEUED, ALB_RUNNING, ALB_DONE, ALB_FAILED = 0, 1, 2, 3
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -87,6 +126,30 @@ _SIGS = {
                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "alb_velocities": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "alb_batch_variants": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "alb_batch_create": (ctypes.c_int, [ctypes.POINTER(alb_config), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "alb_batch_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "alb_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "alb_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "alb_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "alb_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(alb_batch_tuning)]),
+    "alb_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(alb_batch_tuning)]),
+    "alb_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "alb_server_config_default": (ctypes.c_int, [ctypes.POINTER(alb_server_config)]),
+    "alb_server_create": (ctypes.c_int, [ctypes.POINTER(alb_server_config),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "alb_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(alb_request),
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "alb_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(alb_result)]),
+    "alb_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "alb_server_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(alb_server_stats)]),
+    "alb_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -242,18 +305,72 @@ def alb_velocities():
     return x, y
 
 
-class Flow:
-    """One flow on the GPU (owns an alb_handle). Fields are (ny, nx) arrays."""
+def alb_batch_variants(precision):
+    """[(block, min_blocks), ...] of the compiled batched-kernel variants."""
+    n = ctypes.c_int()
+    block = np.zeros(8, np.int32)
+    minb = np.zeros(8, np.int32)
+    _check(lib().alb_batch_variants(int(precision), ctypes.byref(n), block.ctypes.data,
+                                    minb.ctypes.data))
+    return [(int(block[v]), int(minb[v])) for v in range(n.value)]
 
-    def __init__(self, nx, ny, **cfg):
+
+def alb_batch_create(cfgs, stream=None):
+    arr = (alb_config * len(cfgs))(*cfgs)
+    b = ctypes.c_void_p()
+    _check(lib().alb_batch_create(arr, len(cfgs), _stream(stream), ctypes.byref(b)))
+    return b
+
+
+def alb_batch_flow(b, i):
+    h = ctypes.c_void_p()
+    _check(lib().alb_batch_flow(b, int(i), ctypes.byref(h)))
+    return h
+
+
+def alb_batch_step(b, nsteps):
+    return _check(lib().alb_batch_step(b, int(nsteps)))
+
+
+def alb_batch_sync(b, timeout_ms=-1):
+    return _check(lib().alb_batch_sync(b, int(timeout_ms)))
+
+
+def alb_batch_tune(b, trials=3):
+    return _check(lib().alb_batch_tune(b, int(trials)))
+
+
+def alb_batch_get_tuning(b, precision) -> dict:
+    t = alb_batch_tuning()
+    _check(lib().alb_batch_get_tuning(b, int(precision), ctypes.byref(t)))
+    return {"variant": t.variant, "tile_w": list(t.tile_w), "dynamic": t.dynamic,
+            "blocks_per_sm": t.blocks_per_sm}
+
+
+def alb_batch_set_tuning(b, precision, variant=0, tile_w=(64, 128, 128), dynamic=1,
+                         blocks_per_sm=0):
+    t = alb_batch_tuning(variant, (ctypes.c_int * 3)(*tile_w), dynamic, blocks_per_sm)
+    return _check(lib().alb_batch_set_tuning(b, int(precision), ctypes.byref(t)))
+
+
+def alb_batch_destroy(b):
+    return _check(lib().alb_batch_destroy(b))
+
+
+class Flow:
+    """One flow on the GPU. Fields are (ny, nx) arrays. Owns its alb_handle,
+    unless it wraps a flow of a batch (`handle` given), which the batch owns."""
+
+    def __init__(self, nx, ny, handle=None, **cfg):
         self.cfg = alb_config_default(nx=nx, ny=ny, **cfg)
         self.nx, self.ny = nx, ny
-        self.h = alb_create(self.cfg)
+        self.owned = handle is None
+        self.h = alb_create(self.cfg) if handle is None else handle
 
     def close(self):
-        if getattr(self, "h", None) is not None and self.h.value:
+        if getattr(self, "h", None) is not None and self.h.value and self.owned:
             alb_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -288,3 +405,133 @@ class Flow:
 
     def totals(self):
         return alb_totals(self.h)
+
+
+class Batch:
+    """Many flows advanced together (alb_batch_*). specs: list of dicts with
+    nx, ny and alb_config fields; flows[i] is a Flow wrapping flow i."""
+
+    def __init__(self, specs, stream=None):
+        cfgs = [alb_config_default(**sp) for sp in specs]
+        self.b = alb_batch_create(cfgs, stream)
+        self.flows = [Flow(sp["nx"], sp["ny"], handle=alb_batch_flow(self.b, i),
+                           **{k: v for k, v in sp.items() if k not in ("nx", "ny")})
+                      for i, sp in enumerate(specs)]
+
+    def step(self, n):
+        return alb_batch_step(self.b, n)
+
+    def sync(self, timeout_ms=-1):
+        return alb_batch_sync(self.b, timeout_ms)
+
+    def tune(self, trials=3):
+        return alb_batch_tune(self.b, trials)
+
+    def tuning(self, precision):
+        return alb_batch_get_tuning(self.b, precision)
+
+    def set_tuning(self, precision, **kw):
+        return alb_batch_set_tuning(self.b, precision, **kw)
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            for f in self.flows:
+                f.h = None
+            alb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (alb_server_*, alb_submit, alb_poll). submit() takes host
+    fields (copied at once) or a fill(rho, rhoux, rhouy, rhoE) callable that
+    writes (ny, nx) float64 views at admission on the worker thread."""
+
+    def __init__(self, **kw):
+        c = alb_server_config()
+        _check(lib().alb_server_config_default(ctypes.byref(c)))
+        for k, v in kw.items():
+            setattr(c, k, v)
+        self.s = ctypes.c_void_p()
+        _check(lib().alb_server_create(ctypes.byref(c), ctypes.byref(self.s)))
+        self._meta = {}  # id -> (nx, ny, keep, callback keep-alive)
+
+    def submit(self, nsteps, fields=None, fill=None, keep_result=True, **cfg):
+        c = alb_config_default(**cfg)
+        r = alb_request()
+        r.cfg = c
+        r.nsteps = int(nsteps)
+        r.keep_result = 1 if keep_result else 0
+        keep_alive = None
+        if fields is not None:
+            arrs = [np.ascontiguousarray(a, np.float64).ravel() for a in fields]
+            r.rho, r.rhoux, r.rhouy, r.rhoE = [a.ctypes.data for a in arrs]
+            keep_alive = arrs
+        else:
+            nx, ny = c.nx, c.ny
+
+            def _fill(user, a, b, cc, d):
+                try:
+                    outs = [np.ctypeslib.as_array(p, shape=(ny, nx)) for p in (a, b, cc, d)]
+                    fill(*outs)
+                    return 0
+                except Exception:
+                    return 1
+            keep_alive = FILL_FN(_fill)
+            r.fill = keep_alive
+        rid = ctypes.c_uint64()
+        _check(lib().alb_submit(self.s, ctypes.byref(r), ctypes.byref(rid)))
+        self._meta[rid.value] = (c.nx, c.ny, keep_result,
+                                 keep_alive if fields is None else None)
+        return rid.value
+
+    def poll(self, rid):
+        """(state, result) with result a dict once DONE or FAILED, else None."""
+        if rid not in self._meta:  # collected already or never submitted
+            st = ctypes.c_int()
+            _check(lib().alb_poll(self.s, ctypes.c_uint64(rid), ctypes.byref(st), None))
+        nx, ny, keep, _ = self._meta[rid]
+        st = ctypes.c_int()
+        res = alb_result()
+        outs = None
+        if keep:
+            outs = [np.empty((ny, nx)) for _ in range(4)]
+            res.rho, res.rhoux, res.rhouy, res.rhoE = [a.ctypes.data for a in outs]
+        _check(lib().alb_poll(self.s, ctypes.c_uint64(rid), ctypes.byref(st), ctypes.byref(res)))
+        if st.value not in (ALB_DONE, ALB_FAILED):
+            return st.value, None
+        del self._meta[rid]
+        out = {"status": res.status, "steps": int(res.steps), "t_submit": res.t_submit,
+               "t_admit": res.t_admit, "t_done": res.t_done,
+               "stats": {k: int(getattr(res.stats, k)) for k, _ in alb_stats._fields_}}
+        if keep:
+            out["moments"] = outs
+        return st.value, out
+
+    def drain(self, timeout_ms=-1):
+        return _check(lib().alb_server_drain(self.s, int(timeout_ms)))
+
+    def stats(self):
+        st = alb_server_stats()
+        _check(lib().alb_server_stats_get(self.s, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in alb_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None) is not None and self.s.value:
+            alb_server_destroy_(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alb_server_destroy_(s):
+    return _check(lib().alb_server_destroy(s))

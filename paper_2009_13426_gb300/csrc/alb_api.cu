@@ -8,7 +8,6 @@
 #include <new>
 #include <thread>
 
-#include "../../include/alb.h"
 #include "alb_internal.h"
 
 using namespace alb;
@@ -37,19 +36,40 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
-struct alb_handle {
-  alb_config cfg;
-  FlowDev dev;
-  cudaStream_t stream;
-  bool own_stream;
-  double* staging;        // 4 * n doubles for host transfers
-  double* tot_partials;   // 4 doubles per chunk of the totals reduction
-  double* tot_out;        // 4 doubles, device result of the totals reduction
-  unsigned long long* ctr_host;
-  double* tot_host;       // pinned copy of tot_out
-  uint64_t steps;
-  bool initialised;
-};
+namespace alb {
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+int handle_destroy(alb_handle* h) {
+  if (!h) return ALB_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->dev.pop[b]);
+    cudaFree(h->dev.mom[b]);
+    cudaFree(h->dev.lat[b]);
+    cudaFree(h->dev.nxt[b]);
+    cudaFree(h->dev.lam[b]);
+  }
+  cudaFree(h->dev.ctr);
+  cudaFree(h->staging);
+  cudaFree(h->tot_partials);
+  cudaFree(h->tot_out);
+  cudaFreeHost(h->ctr_host);
+  cudaFreeHost(h->tot_host);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return ALB_OK;
+}
+
+}  // namespace alb
 
 extern "C" {
 
@@ -115,23 +135,8 @@ static int check_config(const alb_config* c) {
 
 int alb_destroy(alb_handle* h) {
   if (!h) return ALB_OK;
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  for (int b = 0; b < 2; ++b) {
-    cudaFree(h->dev.pop[b]);
-    cudaFree(h->dev.mom[b]);
-    cudaFree(h->dev.lat[b]);
-    cudaFree(h->dev.nxt[b]);
-    cudaFree(h->dev.lam[b]);
-  }
-  cudaFree(h->dev.ctr);
-  cudaFree(h->staging);
-  cudaFree(h->tot_partials);
-  cudaFree(h->tot_out);
-  cudaFreeHost(h->ctr_host);
-  cudaFreeHost(h->tot_host);
-  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
-  delete h;
-  return ALB_OK;
+  if (h->owner) return fail(ALB_EINVAL, "alb_destroy: the handle belongs to a batch or server");
+  return handle_destroy(h);
 }
 
 int alb_create(const alb_config* cfg, alb_handle** out) {
@@ -190,7 +195,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   do {                                                                 \
     cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));              \
     if (e_ != cudaSuccess) {                                           \
-      alb_destroy(h);                                                  \
+      handle_destroy(h);                                               \
       cudaGetLastError();                                              \
       return fail(ALB_ENOMEM, "cudaMalloc of %zu bytes failed: %s", (size_t)(bytes), \
                   cudaGetErrorString(e_));                             \
@@ -210,7 +215,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
 #undef ALLOC
   if (cudaMallocHost((void**)&h->ctr_host, CTR_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMallocHost((void**)&h->tot_host, 4 * sizeof(double)) != cudaSuccess) {
-    alb_destroy(h);
+    handle_destroy(h);
     return fail(ALB_ENOMEM, "pinned host allocation failed");
   }
   *out = h;
@@ -400,3 +405,20 @@ int alb_select_shift(const double* rho, const double* rhou, int n, double n0, in
 }
 
 }  // extern "C"
+
+namespace alb {
+
+int config_check(const alb_config* c) { return check_config(c); }
+
+// Device bytes alb_create allocates for a flow (the same sizes as there).
+size_t flow_device_bytes(const alb_config* c) {
+  const size_t n = (size_t)c->nx * c->ny, ps = (n + 63) / 64 * 64;
+  const size_t es = c->precision == ALB_FP64_PLAIN ? sizeof(double) : sizeof(float);
+  size_t b = 2 * (NPLANES * ps * es + 4 * ps * es + 2 * ps);
+  if (c->precision == ALB_FP32_FORM) b += 2 * NM * ps * sizeof(float);
+  b += CTR_COUNT * sizeof(unsigned long long) + 4 * n * sizeof(double) +
+       (size_t)(totals_blocks((long long)n) + 1) * 4 * sizeof(double) + 4 * sizeof(double);
+  return b;
+}
+
+}  // namespace alb

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/alb.h"
 #include "alb_device.cuh"
 
 namespace alb {
@@ -38,6 +39,32 @@ struct FlowDev {
   int cur;           // buffer holding the current state
 };
 
+// Arguments of one step of one flow: read buffer `in`, write buffer in ^ 1.
+template <typename P>
+struct StepArgs {
+  const P* pop_in;
+  P* pop_out;
+  const P* mom_in;
+  P* mom_out;
+  const uint8_t* lat_in;
+  const uint8_t* nxt_in;
+  uint8_t* lat_out;
+  uint8_t* nxt_out;
+  const float* lam_in;  // FP32 form: multipliers of the previous step (8 planes)
+  float* lam_out;
+  size_t ps;
+  Params prm;
+  unsigned long long* ctr;
+};
+
+template <typename P>
+inline StepArgs<P> step_args(const FlowDev& f, int in) {
+  const int out = in ^ 1;
+  return StepArgs<P>{(const P*)f.pop[in], (P*)f.pop[out], (const P*)f.mom[in], (P*)f.mom[out],
+                     f.lat[in], f.nxt[in], f.lat[out], f.nxt[out], f.lam[in], f.lam[out],
+                     f.ps, f.prm, f.ctr};
+}
+
 // Global totals (alb_totals.cu): one block per chunk of TOT_CHUNK nodes writes
 // 4 partial sums; a single block adds them in order.
 constexpr int TOT_THREADS = 256;
@@ -66,4 +93,48 @@ cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s);
 cudaError_t launch_select(const double* rho, const double* rhou, int n, double n0, int umax,
                           signed char* out, cudaStream_t s);
 
+// Batched step (alb_batch_f32.cu, alb_batch_f64.cu). A work item is a tile of
+// 2^tw_log2 x (block >> tw_log2) nodes of flow `flow` with origin (x0, y0).
+struct WorkItem {
+  int flow, x0, y0, tw_log2;
+};
+// Compiled variants of the batched kernel per precision.
+struct BatchVariant {
+  int block, min_blocks;
+};
+int batch_variant_count(int precision);
+BatchVariant batch_variant(int precision, int v);
+cudaError_t launch_flip(int* cur, int n, cudaStream_t s);
+
+// Error reporting of the C ABI (alb_api.cu): sets the thread's message and
+// returns code.
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+}  // namespace alb
+
+// State behind an alb_handle (alb_api.cu). A handle that belongs to a batch or
+// a server (owner != null) is destroyed with its owner.
+struct alb_handle {
+  alb_config cfg;
+  alb::FlowDev dev;
+  cudaStream_t stream;
+  bool own_stream;
+  double* staging;        // 4 * n doubles for host transfers
+  double* tot_partials;   // 4 doubles per chunk of the totals reduction
+  double* tot_out;        // 4 doubles, device result of the totals reduction
+  unsigned long long* ctr_host;
+  double* tot_host;       // pinned copy of tot_out
+  uint64_t steps;
+  bool initialised;
+  const void* owner;
+};
+
+namespace alb {
+// Frees a handle whatever its owner (alb_api.cu).
+int handle_destroy(alb_handle* h);
+// Validation of alb_create (ALB_OK or an error code with the message set).
+int config_check(const alb_config* c);
+// Device bytes alb_create allocates for a flow of this configuration.
+size_t flow_device_bytes(const alb_config* c);
 }  // namespace alb

@@ -238,15 +238,11 @@ cudaError_t launch_step(FlowDev& f, cudaStream_t s) {
   const int in = f.cur, out = f.cur ^ 1;
   cudaError_t e;
   if (f.precision == 0) {
-    StepArgs<double> a{(const double*)f.pop[in], (double*)f.pop[out], (const double*)f.mom[in],
-                       (double*)f.mom[out], f.lat[in], f.nxt[in], f.lat[out], f.nxt[out],
-                       nullptr, nullptr, f.ps, f.prm, f.ctr};
+    const StepArgs<double> a = step_args<double>(f, in);
     if ((e = allow_smem(step_kernel<double>, smem_bytes<double>())) != cudaSuccess) return e;
     step_kernel<double><<<grid_of(f.prm), BLOCK, smem_bytes<double>(), s>>>(a);
   } else {
-    StepArgs<float> a{(const float*)f.pop[in], (float*)f.pop[out], (const float*)f.mom[in],
-                      (float*)f.mom[out], f.lat[in], f.nxt[in], f.lat[out], f.nxt[out],
-                      f.lam[in], f.lam[out], f.ps, f.prm, f.ctr};
+    const StepArgs<float> a = step_args<float>(f, in);
     if ((e = allow_smem(step_kernel<float>, smem_bytes<float>())) != cudaSuccess) return e;
     step_kernel<float><<<grid_of(f.prm), BLOCK, smem_bytes<float>(), s>>>(a);
   }

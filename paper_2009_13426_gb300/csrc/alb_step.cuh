@@ -76,23 +76,6 @@ struct Acc<float> {
   __device__ __forceinline__ float valf() const { return s + c; }
 };
 
-template <typename P>
-struct StepArgs {
-  const P* pop_in;
-  P* pop_out;
-  const P* mom_in;
-  P* mom_out;
-  const uint8_t* lat_in;
-  const uint8_t* nxt_in;
-  uint8_t* lat_out;
-  uint8_t* nxt_out;
-  const float* lam_in;  // FP32 form: multipliers of the previous step (8 planes)
-  float* lam_out;
-  size_t ps;
-  Params prm;
-  unsigned long long* ctr;
-};
-
 // Multipliers stored for node k (8 planes), moved into the frame of lattice
 // (Ux, Uy) from the lattice code they were computed in.
 __device__ __forceinline__ void load_warm(const float* lam, size_t ps, size_t k, int code_from,

@@ -150,12 +150,12 @@ class FlowSpec:
             if u_inf > 2.5 - swirl:
                 u_inf = 2.5 - swirl
             mach = u_inf / math.sqrt(gamma * T_inf)
-            r = max(2.0, min(self.nx, self.ny) / 12.8)
+            r = max(5.0, min(self.nx, self.ny) / 12.8)
             return isentropic_vortex(self.nx, self.ny, strength=5.0, radius=r, mach=mach,
                                      T_inf=T_inf, seed=self.seed, gamma=gamma)
         if self.kind == "shear":
             return shear_layer(self.nx, mach=self.mach, T_cold=0.35, T_ratio=self.T_ratio,
-                               delta=max(2.0, self.nx / 512.0), seed=self.seed, gamma=gamma,
+                               delta=8.0, seed=self.seed, gamma=gamma,
                                ny=self.ny)
         if self.kind == "riemann2d":
             return riemann_2d(self.nx, gamma)

@@ -1,0 +1,163 @@
+"""Batched flows (alb_batch_*): many flows of uneven size in one launch per
+step must give, flow by flow, exactly what each flow gives alone through
+alb_step: the per-node update is the same code and reads only its own flow,
+so every kernel variant, tile shape and work distribution must agree bit for
+bit, and so must the counters."""
+import numpy as np
+import pytest
+
+from paper_2009_13426_gb300 import flows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FS = flows.FlowSpec
+# small (nx < 128), medium (nx < 512) and large flows, both precisions
+SPECS = [
+    FS("vortex", 40, 24, 1.2, 2.0, 1e-3, 0, "fp32", seed=11),
+    FS("shear", 64, 64, 2.0, 3.0, 1e-4, 0, "fp32", seed=12),
+    FS("shear", 136, 20, 1.5, 2.0, 1e-5, 0, "fp32", seed=13),
+    FS("shear", 520, 8, 2.2, 3.0, 1e-4, 0, "fp32", seed=16),
+    FS("vortex", 49, 41, 1.0, 1.5, 1e-3, 0, "fp64", seed=14),
+    FS("shear", 96, 40, 2.5, 3.0, 1e-4, 0, "fp64", seed=15),
+]
+STEPS = 7  # three graph replays of two steps, then one single step
+
+
+@pytest.fixture(scope="module")
+def alb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_13426_gb300 import alb as A
+    A.lib()
+    return A
+
+
+def cfg_of(alb, sp):
+    prec = alb.ALB_FP32_FORM if sp.precision == "fp32" else alb.ALB_FP64_PLAIN
+    return dict(nx=sp.nx, ny=sp.ny, nu=sp.nu, precision=prec)
+
+
+def state(fl):
+    return fl.moments(), fl.shifts()
+
+
+def alone(alb, sp, steps):
+    fl = alb.Flow(**cfg_of(alb, sp))
+    assert fl.init(*sp.fields()) == alb.ALB_OK
+    fl.step(steps)
+    fl.sync()
+    out = state(fl), fl.stats()
+    fl.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def reference(alb):
+    return {k: {n: alone(alb, sp, n) for n in (2, 3, STEPS)} for k, sp in enumerate(SPECS)}
+
+
+def init_all(batch):
+    for sp, fl in zip(SPECS, batch.flows):
+        fl.init(*sp.fields())
+
+
+def assert_same(got, ref, what):
+    (m, s), (M, S) = got, ref
+    for a, b in zip(m, M):
+        assert np.array_equal(a, b), what
+    for a, b in zip(s, S):
+        assert np.array_equal(a, b), what
+
+
+def test_batch_equals_alone_bit_for_bit(alb, reference):
+    b = alb.Batch([cfg_of(alb, sp) for sp in SPECS])
+    try:
+        init_all(b)
+        b.step(STEPS)
+        b.sync()
+        for k, fl in enumerate(b.flows):
+            assert_same(state(fl), reference[k][STEPS][0], "flow %d" % k)
+            st, ref = fl.stats(), reference[k][STEPS][1]
+            assert st == ref, (k, st, ref)
+    finally:
+        b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_every_variant_and_tile_shape_agrees(alb, reference, prec):
+    P = alb.ALB_FP32_FORM if prec == "fp32" else alb.ALB_FP64_PLAIN
+    b = alb.Batch([cfg_of(alb, sp) for sp in SPECS])
+    try:
+        for v, (block, _) in enumerate(alb.alb_batch_variants(P)):
+            for tw, dyn in ((8, 0), (min(32, block), 1), (block, 1)):
+                b.set_tuning(P, variant=v, tile_w=(tw, tw, tw), dynamic=dyn)
+                assert b.tuning(P)["variant"] == v
+                init_all(b)
+                b.step(STEPS)
+                b.sync()
+                for k, (sp, fl) in enumerate(zip(SPECS, b.flows)):
+                    if sp.precision == prec:
+                        assert_same(state(fl), reference[k][STEPS][0],
+                                    "flow %d variant %d tile %d dynamic %d" % (k, v, tw, dyn))
+    finally:
+        b.close()
+
+
+def test_tuner_leaves_state_and_counters_alone(alb, reference):
+    b = alb.Batch([cfg_of(alb, sp) for sp in SPECS])
+    try:
+        init_all(b)
+        b.step(3)
+        b.sync()
+        before = [(state(fl), fl.stats()) for fl in b.flows]
+        b.tune(trials=1)
+        for k, fl in enumerate(b.flows):
+            assert_same(state(fl), before[k][0], "flow %d after tuning" % k)
+            assert fl.stats() == before[k][1]
+            assert_same(state(fl), reference[k][3][0], "flow %d" % k)
+        for P in (alb.ALB_FP32_FORM, alb.ALB_FP64_PLAIN):
+            t = b.tuning(P)
+            block = alb.alb_batch_variants(P)[t["variant"]][0]
+            assert all(8 <= w <= block for w in t["tile_w"])
+        b.step(STEPS - 3)
+        b.sync()
+        for k, fl in enumerate(b.flows):
+            assert_same(state(fl), reference[k][STEPS][0], "flow %d tuned" % k)
+    finally:
+        b.close()
+
+
+def test_flow_stepped_alone_inside_a_batch(alb, reference):
+    """A batch flow's own handle steps it alone; the batch picks up its
+    buffer parity at the next batched step."""
+    b = alb.Batch([cfg_of(alb, sp) for sp in SPECS])
+    try:
+        init_all(b)
+        b.flows[0].step(1)
+        b.step(2)
+        b.sync()
+        assert_same(state(b.flows[0]), reference[0][3][0], "flow 0")
+        for k in range(1, len(SPECS)):
+            assert_same(state(b.flows[k]), reference[k][2][0], "flow %d" % k)
+    finally:
+        b.close()
+
+
+def test_batch_errors(alb):
+    b = alb.Batch([cfg_of(alb, sp) for sp in SPECS[:2]])
+    try:
+        with pytest.raises(alb.AlbError) as ei:
+            b.step(1)  # not initialised
+        assert ei.value.code == alb.ALB_EINVAL
+        with pytest.raises(alb.AlbError) as ei:
+            alb.alb_destroy(b.flows[0].h)  # owned by the batch
+        assert ei.value.code == alb.ALB_EINVAL
+        with pytest.raises(alb.AlbError):
+            b.set_tuning(alb.ALB_FP32_FORM, variant=99)
+        with pytest.raises(alb.AlbError):
+            b.set_tuning(alb.ALB_FP32_FORM, variant=0, tile_w=(12, 64, 64))
+        with pytest.raises(alb.AlbError):
+            alb.alb_batch_flow(b.b, 5)
+    finally:
+        b.close()
