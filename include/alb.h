@@ -210,8 +210,8 @@ int alb_equilibrium(const double* rho, const double* ubx, const double* uby, con
                     int* iters, int* status, void* stream);
 
 /* out[k] = exp(-s[k]) by the table-driven FP64 exponential that the FP32
- * form's equilibrium uses (Tang's method: 32-entry table of 2^(j/32), degree-6
- * polynomial on |r| <= ln2/64). 0 below 2^-1022, +inf from 2^1024 on. Device
+ * form's equilibrium uses (Tang's method: 256-entry table of 2^(j/256), degree-4
+ * polynomial on |r| <= ln2/512). 0 below 2^-1022, +inf from 2^1024 on. Device
  * arrays of n doubles. Exposed so that its accuracy can be checked. */
 int alb_exp_neg(const double* s, int n, double* out, void* stream);
 
@@ -386,6 +386,8 @@ typedef struct {
   uint64_t budget_bytes;       /* admission budget */
   double busy_seconds;         /* wall time spent running chunks */
   double elapsed_seconds;      /* since creation */
+  double ns_per_update[2];     /* measured time of one node update, [0] FP64
+                                  plain, [1] FP32 form (smoothed over chunks) */
 } alb_server_stats;
 
 /* Fill *c with the defaults above. */

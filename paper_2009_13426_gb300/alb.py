@@ -95,7 +95,8 @@ class alb_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "submitted", "admitted", "completed", "failed", "queued", "running", "node_updates",
         "chunks", "steps", "resident_bytes", "budget_bytes")] + [
-        ("busy_seconds", ctypes.c_double), ("elapsed_seconds", ctypes.c_double)]
+        ("busy_seconds", ctypes.c_double), ("elapsed_seconds", ctypes.c_double),
+        ("ns_per_update", ctypes.c_double * 2)]
 
 
 ALB_QUEUED, ALB_RUNNING, ALB_DONE, ALB_FAILED = 0, 1, 2, 3
@@ -519,7 +520,9 @@ class Server:
     def stats(self):
         st = alb_server_stats()
         _check(lib().alb_server_stats_get(self.s, ctypes.byref(st)))
-        return {k: getattr(st, k) for k, _ in alb_server_stats._fields_}
+        out = {k: getattr(st, k) for k, _ in alb_server_stats._fields_}
+        out["ns_per_update"] = list(st.ns_per_update)
+        return out
 
     def close(self):
         if getattr(self, "s", None) is not None and self.s.value:

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(B, MINB)
   static_assert(sizeof(StepArgs<P>) % 8 == 0, "step arguments copy as 8-byte words");
   static_assert(sizeof(StepArgs<P>) / 8 <= B, "one word per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_tab[32];
+  __shared__ double s_tab[EXPT_N];
   __shared__ __align__(16) unsigned long long s_args[sizeof(StepArgs<P>) / 8];
   __shared__ int s_item;
   load_exptab(s_tab);

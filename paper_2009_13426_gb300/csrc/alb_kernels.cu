@@ -23,7 +23,7 @@ template <typename P>
 __global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1))
     step_kernel(StepArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_tab[32];
+  __shared__ double s_tab[EXPT_N];
   load_exptab(s_tab);
   const Columns<P, BLOCK> cl(smem_raw);
   const int x = blockIdx.x * BLOCK + threadIdx.x;
@@ -61,7 +61,7 @@ __device__ __forceinline__ void init_prim(const double* rho, const double* rhoux
 template <typename P>
 __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_tab[32];
+  __shared__ double s_tab[EXPT_N];
   load_exptab(s_tab);
   const Columns<P, BLOCK> cl(smem_raw);
   const Params& pr = a.prm;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(BLOCK)
     equilibrium_kernel(const double* rho, const double* ubx, const double* uby, const double* T,
                        int n, double tol, int maxit, int precision, double* feq, double* lambda,
                        int* iters, int* status) {
-  __shared__ double s_tab[32];
+  __shared__ double s_tab[EXPT_N];
   __shared__ double s_eq[Q * BLOCK];
   load_exptab(s_tab);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BLOCK)
 }
 
 __global__ void exp_neg_kernel(const double* s, int n, double* out) {
-  __shared__ double s_tab[32];
+  __shared__ double s_tab[EXPT_N];
   load_exptab(s_tab);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) out[k] = exp_neg(s[k], s_tab);

@@ -11,9 +11,9 @@
 // FP32 phase or the refinement fails, the full FP64 Newton takes over.
 //
 // The FP64 exponential is table-driven (Tang, ACM TOMS 15(2), 1989):
-// exp(-s) = 2^(n/32) exp(r), n = round(-32 s / ln 2), |r| <= ln2/64, with
-// 2^(j/32) from a 32-entry table and exp(r) by its degree-6 Taylor polynomial
-// (constants in exp_table.h, generated by gen_exp_table.py).
+// exp(-s) = 2^(n/256) exp(r), n = round(-256 s / ln 2), |r| <= ln2/512, with
+// 2^(j/256) from a 256-entry table and exp(r) by its degree-4 Taylor
+// polynomial (constants in exp_table.h, generated by gen_exp_table.py).
 //
 // Every pass over the velocities streams through the symmetric groups of the
 // D2Q21 set (the rest velocity, the axis pairs +-a, the diagonal quadruples):
@@ -71,17 +71,22 @@ __device__ __forceinline__ void visit_groups(const R l[NM], V& v) {
   }
 }
 
-// 2^(j/32), j = 0..31; kernels copy it to shared memory (lanes index it freely).
-static __constant__ double c_exptab[32] = {ALB_EXPT_TABLE_VALUES};
+// 2^(j/N), j = 0..N-1 (N = EXPT_N); kernels copy it to shared memory (lanes
+// index it freely).
+static __constant__ double c_exptab[EXPT_N] = {ALB_EXPT_TABLE_VALUES};
 
-// Copy the table into a block's shared array (all threads; includes a barrier).
+// Copy the table into a block's shared array of EXPT_N doubles (all threads;
+// includes a barrier).
 __device__ __forceinline__ void load_exptab(double* s_tab) {
-  if (threadIdx.x < 32) s_tab[threadIdx.x] = c_exptab[threadIdx.x];
+  for (int j = threadIdx.x; j < EXPT_N; j += blockDim.x) s_tab[j] = c_exptab[j];
   __syncthreads();
 }
 
-// Table-driven FP64 exp(-s); tab = 2^(j/32), j = 0..31 (in shared memory).
-// Returns 0 below 2^-1022 (no subnormal results) and +inf from 2^1024 on.
+// Table-driven FP64 exp(-s) (Tang's method with an N = 256 table): n nearest
+// to -s N / ln2, r = -s - n ln2/N in two parts (|r| <= ln2/512), exp(r) by its
+// degree-4 Taylor polynomial, times 2^(n/N) = 2^(n >> 8) tab[n & 255].
+// 9 FP64 operations. Returns 0 below 2^-1022 (no subnormal results) and +inf
+// from 2^1024 on.
 __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer
   const double t = fma(-s, EXPT_INV_L, shifter);
@@ -89,14 +94,13 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   const double nd = t - shifter;
   double r = fma(nd, -EXPT_L_HI, -s);
   r = fma(nd, -EXPT_L_LO, r);
-  double q = fma(r, EXPT_C6, EXPT_C5);
-  q = fma(q, r, EXPT_C4);
-  q = fma(q, r, EXPT_C3);
+  double q = fma(r, EXPT_C4, EXPT_C3);
   q = fma(q, r, EXPT_C2);
   q = fma(q, r, 1.0);
   q = fma(q, r, 1.0);
-  const int e = n >> 5;
-  const long long bits = __double_as_longlong(tab[n & 31]) + ((long long)e << 52);
+  const int e = n >> EXPT_BITS;
+  const long long bits =
+      __double_as_longlong(tab[n & (EXPT_N - 1)]) + ((long long)e << 52);
   double sc = __longlong_as_double(bits);
   sc = e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : sc);
   return q * sc;

@@ -531,6 +531,8 @@ int alb_server_stats_get(alb_server* s, alb_server_stats* out) {
   out->resident_bytes = s->resident;
   out->budget_bytes = s->budget;
   out->elapsed_seconds = s->now();
+  out->ns_per_update[0] = s->ms_per_update[0] * 1e6;
+  out->ns_per_update[1] = s->ms_per_update[1] * 1e6;
   return ALB_OK;
 }
 

@@ -1,15 +1,16 @@
 """Generate csrc/exp_table.h: constants of the table-driven FP64 exponential.
 
 Method (P. T. P. Tang, "Table-driven implementation of the exponential
-function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
-exp(x) = 2^(n/32) * exp(r) with n = round(32 x / ln 2) and
-r = x - n ln2/32, |r| <= ln2/64; 2^(n/32) = 2^(n >> 5) * T[n & 31] with
-T[j] = 2^(j/32); exp(r) by its Taylor polynomial of degree 6 (remainder
-below r^7/7! < 4e-18 on |r| <= ln2/64).
+function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989), with a
+table of N = 2^BITS = 256 entries:
+exp(x) = 2^(n/N) * exp(r) with n = round(N x / ln 2) and
+r = x - n ln2/N, |r| <= ln2/(2N); 2^(n/N) = 2^(n >> BITS) * T[n & (N-1)] with
+T[j] = 2^(j/N); exp(r) by its Taylor polynomial of degree DEG = 4 (remainder
+below r^5/5! < 4e-17 on |r| <= ln2/512).
 
 Every constant is computed here with 60-digit decimal arithmetic and rounded
-to the nearest double: T[j], 32/ln2, the two-part split of ln2/32 (high part
-with 38 significant bits so that n * high is exact for |n| < 2^15) and 1/k!.
+to the nearest double: T[j], N/ln2, the two-part split of ln2/N (high part
+with 33 significant bits so that n * high is exact for |n| < 2^20) and 1/k!.
 Run: python gen_exp_table.py > exp_table.h
 """
 from decimal import Decimal, getcontext
@@ -45,35 +46,44 @@ def hexd(x):
     return float(x).hex()
 
 
+BITS = 8
+N = 1 << BITS
+DEG = 4
+HI_BITS = 33
+
+
 def main():
     ln2 = d_ln2()
-    L = ln2 / 32
-    inv_l = 32 / ln2
-    # high part of L with 38 significant bits
+    L = ln2 / N
+    inv_l = N / ln2
+    # high part of L with HI_BITS significant bits
     f = float(L)
     m, e = __import__("math").frexp(f)
-    scale = 2 ** 38
+    scale = 2 ** HI_BITS
     hi = round(m * scale) / scale
     hi = __import__("math").ldexp(hi, e)
     lo = float(L - Decimal(hi))
-    table = [float(d_exp(Decimal(j) * ln2 / 32)) for j in range(32)]
-    fact = [float(Decimal(1) / Decimal(__import__("math").factorial(k))) for k in range(7)]
+    table = [float(d_exp(Decimal(j) * ln2 / N)) for j in range(N)]
+    fact = [float(Decimal(1) / Decimal(__import__("math").factorial(k))) for k in range(DEG + 1)]
     out = []
     out.append("// Generated by gen_exp_table.py: constants of the table-driven FP64")
     out.append("// exponential (Tang's method), each computed with 60-digit decimal")
     out.append("// arithmetic and rounded to the nearest double.")
     out.append("#pragma once")
     out.append("namespace alb {")
-    out.append("constexpr double EXPT_INV_L = %s;  // 32 / ln 2" % hexd(inv_l))
-    out.append("constexpr double EXPT_L_HI = %s;   // ln2/32, 38 significant bits" % hexd(hi))
-    out.append("constexpr double EXPT_L_LO = %s;   // ln2/32 - EXPT_L_HI" % hexd(lo))
-    for k in range(2, 7):
+    out.append("constexpr int EXPT_BITS = %d;  // table of 2^EXPT_BITS entries" % BITS)
+    out.append("constexpr int EXPT_N = %d;" % N)
+    out.append("constexpr double EXPT_INV_L = %s;  // %d / ln 2" % (hexd(inv_l), N))
+    out.append("constexpr double EXPT_L_HI = %s;   // ln2/%d, %d significant bits"
+               % (hexd(hi), N, HI_BITS))
+    out.append("constexpr double EXPT_L_LO = %s;   // ln2/%d - EXPT_L_HI" % (hexd(lo), N))
+    for k in range(2, DEG + 1):
         out.append("constexpr double EXPT_C%d = %s;  // 1/%d!" % (k, hexd(fact[k]), k))
     out.append("}  // namespace alb")
-    out.append("// T[j] = 2^(j/32), j = 0..31, as an initializer list")
+    out.append("// T[j] = 2^(j/%d), j = 0..%d, as an initializer list" % (N, N - 1))
     out.append("#define ALB_EXPT_TABLE_VALUES \\")
-    for j in range(0, 32, 2):
-        tail = ", \\" if j < 30 else ""
+    for j in range(0, N, 2):
+        tail = ", \\" if j < N - 2 else ""
         out.append("    %s, %s%s" % (hexd(table[j]), hexd(table[j + 1]), tail))
     print("\n".join(out))
 
