@@ -12,7 +12,20 @@ form's moment error against it), the end-to-end figure through the C ABI with
 host buffers, the FP64-pipe roofline of the step kernel, and the CPU oracle
 on a bounded sample of the same flow.
 
-`--impl reference` times the CPU oracle instead (see DESIGN.md).
+Two sub-results run after it on one GPU (skipped under torchrun with N > 1):
+
+* "batched": 256 independent periodic flows, sides log-uniform in
+  [64, 1024] (vortex or shear layer, Mach 0.5-3, temperature ratio 1-4,
+  nu 1e-5..1e-3, FP32 form), advanced together by one persistent launch per
+  step (alb_batch_step: CUDA graph of two steps, autotuned launch shape);
+  MLUPS over all flows, beside the same flows stepped one launch per flow.
+* "serve": the serving loop under a Poisson stream of requests (50 per
+  second for 60 s; sides 64-2048, 100-5000 steps, FP32 or FP64 form, vortex,
+  shear-layer or 2D-Riemann initial data): completion latency p50/p99,
+  served versus offered node updates; then a second stream at about 70 %
+  of the measured capacity, drained to completion (bounded).
+
+`--impl reference` times the CPU oracle instead.
 Multi-GPU (torchrun, N ranks): every rank runs its own replica (weak scaling).
 """
 from __future__ import annotations
@@ -51,6 +64,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-drain", type=float, default=90.0,
+                    help="seconds the 70%% run may take after its last arrival")
     return ap.parse_args()
 
 
@@ -202,6 +221,164 @@ def run_reference(args, world, rank):
 
 # ----------------------------------------------------------------- our arm
 
+def _sync_flagged(obj, alb):
+    """Synchronise; node failures are counted flags, not errors."""
+    try:
+        obj.sync()
+    except alb.AlbError as e:
+        if e.code != alb.ALB_ENEWTON:
+            raise
+
+
+def run_batched(args):
+    """256 flows in one persistent launch per step (alb_batch_step)."""
+    import torch
+    from paper_2009_13426_gb300 import alb
+
+    specs = flows.batched_flows(256)
+    nodes = sum(sp.nx * sp.ny for sp in specs)
+    stream = torch.cuda.Stream()
+    b = alb.Batch([dict(nx=sp.nx, ny=sp.ny, nu=sp.nu, precision=alb.ALB_FP32_FORM)
+                   for sp in specs], stream=stream)
+    try:
+        for sp, fl in zip(specs, b.flows):
+            fl.init(*sp.fields())
+        t = time.perf_counter()
+        b.tune(trials=2)
+        tune_s = time.perf_counter() - t
+        tuning = b.tuning(alb.ALB_FP32_FORM)
+        b.step(args.warmup)
+        _sync_flagged(b, alb)
+        s0 = [fl.stats() for fl in b.flows]
+        k = args.batched_steps
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        _sync_flagged(b, alb)
+        s1 = [fl.stats() for fl in b.flows]
+        tot = {key: sum(x[key] - y[key] for x, y in zip(s1, s0))
+               for key in ("fp64_evaluations", "fp32_iterations", "newton_calls",
+                           "reconstructions", "newton_failures", "reconstruction_failures")}
+        # the same flows one launch per flow and step (alb_step), same stream
+        e0.record(stream)
+        for fl in b.flows:
+            fl.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_alone = e0.elapsed_time(e1)
+    finally:
+        b.close()
+    launches = k * (2 if tuning["dynamic"] else 1) + (k % 2)
+    upd = nodes * k
+    return {"workload": "256 periodic flows, side log-uniform 64-1024 (seed 4), vortex or "
+                        "shear layer, Mach 0.5-3, T ratio 1-4, nu 1e-5..1e-3, FP32 form",
+            "flows": len(specs), "nodes": nodes, "steps": k, "unit": UNIT,
+            "value": round(upd / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms / k, 3),
+            "one_launch_per_flow": {"value": round(upd / (ms_alone * 1e-3) / 1e6, 2),
+                                    "launches_per_step": len(specs)},
+            "graph": "two steps per CUDA graph replay",
+            "launches": launches, "tuning": tuning, "tune_seconds": round(tune_s, 1),
+            "per_node": {key: round(v / upd, 4) for key, v in tot.items()
+                         if key not in ("newton_failures", "reconstruction_failures")},
+            "failures": {"node": tot["newton_failures"],
+                         "rebuild": tot["reconstruction_failures"]}}
+
+
+def _serve_stream(alb, reqs, window, drain):
+    """Submit reqs at their arrival times (fields produced at admission by a
+    fill callback), wait `drain` seconds after the window, collect."""
+    srv = alb.Server()
+    ids = {}
+    rejected = 0
+
+    def fill_of(sp):
+        def fill(*outs):
+            for o, f in zip(outs, sp.fields()):
+                o[:] = f
+        return fill
+
+    t0 = time.perf_counter()
+    try:
+        for sp in reqs:
+            while time.perf_counter() - t0 < sp.arrival:
+                time.sleep(0.0005)
+            prec = alb.ALB_FP32_FORM if sp.precision == "fp32" else alb.ALB_FP64_PLAIN
+            try:
+                rid = srv.submit(sp.steps, fill=fill_of(sp), keep_result=False, nx=sp.nx,
+                                 ny=sp.ny, nu=sp.nu, precision=prec)
+                ids[rid] = sp
+            except alb.AlbError:
+                rejected += 1
+        end = t0 + window + drain
+        done = {}
+        while time.perf_counter() < end and len(done) < len(ids):
+            for rid in list(ids):
+                if rid in done:
+                    continue
+                st, res = srv.poll(rid)
+                if res is not None:
+                    done[rid] = res
+            time.sleep(0.05)
+        stats = srv.stats()
+    finally:
+        srv.close()
+    lat = sorted(r["t_done"] - r["t_submit"] for r in done.values())
+    n = len(ids)
+    unfinished = n - len(done)
+
+    def pct(q):
+        # over all submitted requests, unfinished ones counted as slower than any
+        k = int(math.ceil(q * n)) - 1
+        return round(lat[k], 3) if 0 <= k < len(lat) else None
+
+    served = stats["node_updates"]
+    return {"submitted": n, "completed": len(done), "unfinished": unfinished,
+            "rejected": rejected,
+            "p50_s": pct(0.50), "p99_s": pct(0.99),
+            "completed_p50_s": round(lat[len(lat) // 2], 3) if lat else None,
+            "completed_p99_s": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)
+            if lat else None,
+            "offered_updates_per_s": float("%.4g" % (sum(sp.nx * sp.ny * sp.steps for sp in reqs)
+                                                     / window)),
+            "served_mlups": round(served / stats["elapsed_seconds"] / 1e6, 2),
+            "busy_fraction": round(stats["busy_seconds"] / stats["elapsed_seconds"], 3),
+            "elapsed_s": round(stats["elapsed_seconds"], 1),
+            "flagged": sum(1 for r in done.values() if r["status"] == alb.ALB_ENEWTON),
+            "failed": sum(1 for r in done.values()
+                          if r["status"] not in (alb.ALB_OK, alb.ALB_ENEWTON)),
+            "ns_per_update": {"fp64": round(stats["ns_per_update"][0], 3),
+                              "fp32": round(stats["ns_per_update"][1], 3)}}
+
+
+def run_serve(args):
+    from paper_2009_13426_gb300 import alb
+
+    w = args.serve_seconds
+    reqs = flows.serving_requests(rate=50.0, duration=w)
+    heavy = _serve_stream(alb, reqs, w, 5.0)
+    # second stream at ~70 % of the capacity measured in the first one
+    ns = heavy["ns_per_update"]
+    probe = flows.serving_requests(rate=50.0, duration=60.0, seed=6)
+    mean_s = sum(sp.nx * sp.ny * sp.steps * ns["fp32" if sp.precision == "fp32" else "fp64"]
+                 for sp in probe) * 1e-9 / len(probe)
+    rate = 0.7 / mean_s
+    reqs70 = flows.serving_requests(rate=rate, duration=w, seed=7)
+    light = _serve_stream(alb, reqs70, w, args.serve_drain)
+    light["rate_per_s"] = round(rate, 4)
+    return {"workload": "Poisson arrivals, sides log-uniform 64-2048, steps log-uniform "
+                        "100-5000, FP32 or FP64 form, vortex / shear layer / 2D Riemann; "
+                        "fields made at admission; 80 % HBM admission budget",
+            "window_s": w, "rate_50_per_s": heavy, "rate_70pct_capacity": light,
+            "latency": "submit to results in host memory; p50/p99 over all submitted "
+                       "requests (unfinished ones count as slower than any), completed_* "
+                       "over the completed ones"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2009_13426_gb300 import alb
@@ -315,6 +492,12 @@ def run_ours(args, world, rank, local):
         cpu = {"value": round(res["mlups"], 4), "unit": UNIT, "cores": os.cpu_count(),
                "kind": "oracle", "sample": res["sample"]}
 
+    batched = serve = None
+    if world == 1 and not args.no_batched:
+        batched = run_batched(args)
+    if world == 1 and not args.no_serve:
+        serve = run_serve(args)
+
     if rank != 0:
         return
     line = {
@@ -342,6 +525,12 @@ def run_ours(args, world, rank, local):
                                         "newton_failures", "reconstruction_failures")},
     }
     line.update(extra)
+    if batched:
+        line["batched"] = batched
+    if serve:
+        line["serve"] = serve
+    if world > 1:
+        line["batched"] = line["serve"] = "skipped with more than one rank"
     if e2e:
         line["e2e"] = e2e
     if cpu:

@@ -64,6 +64,7 @@ enum { ALB_D2Q21 = 21 };
 enum { ALB_FP64_PLAIN = 0, ALB_FP32_FORM = 1 };
 enum { ALB_PERIODIC = 0, ALB_ZERO_GRADIENT = 1 };
 enum { ALB_HOST = 0, ALB_DEVICE = 1 };
+enum { ALB_START_AUTO = 0, ALB_START_MAXWELLIAN = 1, ALB_START_PREVIOUS = 2 };
 
 typedef struct alb_handle alb_handle; /* opaque */
 
@@ -87,6 +88,14 @@ typedef struct alb_handle alb_handle; /* opaque */
  *                sensor_alpha[2]), constant beyond (sensor_eps increasing).
  *   newton_tol   stop when max_k |G_k| / rho <= newton_tol (paper: 1e-12).
  *   newton_maxit iteration cap.
+ *   newton_start starting point of each equilibrium solve: ALB_START_AUTO
+ *                (the node's multipliers of the previous step in the FP32
+ *                form, the Maxwellian in FP64 plain), ALB_START_MAXWELLIAN,
+ *                or ALB_START_PREVIOUS (the node's, or for a rebuilt pull the
+ *                sender's, multipliers of the previous step moved to the
+ *                lattice of the solve; 8 more planes per buffer). The root is
+ *                unique, so the start changes only the path and round-off;
+ *                ALB_START_MAXWELLIAN follows the oracle's iteration.
  *   stream       cudaStream_t to work on; NULL: the library creates one. */
 typedef struct {
   int nx, ny;
@@ -102,6 +111,7 @@ typedef struct {
   double sensor_alpha[3];
   double newton_tol;
   int newton_maxit;
+  int newton_start;
   void* stream;
 } alb_config;
 
@@ -120,7 +130,8 @@ typedef struct {
 
 /* Fill *cfg with defaults: 64x64, D2Q21, u_max 2, nu 1e-3, gamma 1.4,
  * n0 0.5, FP64 plain, periodic, sensor off (eps 0.01/0.1/1, alpha
- * 1.05/1.35/1.6), tol 1e-12, 50 iterations, library stream. */
+ * 1.05/1.35/1.6), tol 1e-12, 50 iterations, ALB_START_AUTO, library
+ * stream. */
 int alb_config_default(alb_config* cfg);
 
 /* Create a flow: validates cfg and allocates two buffers of 42 population

@@ -34,6 +34,9 @@ ALB_PERIODIC = 0
 ALB_ZERO_GRADIENT = 1
 ALB_HOST = 0
 ALB_DEVICE = 1
+ALB_START_AUTO = 0
+ALB_START_MAXWELLIAN = 1
+ALB_START_PREVIOUS = 2
 Q = 21
 
 
@@ -51,7 +54,7 @@ class alb_config(ctypes.Structure):
         ("bc_y", ctypes.c_int), ("sensor", ctypes.c_int),
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
-        ("stream", ctypes.c_void_p),
+        ("newton_start", ctypes.c_int), ("stream", ctypes.c_void_p),
     ]
 
 

@@ -17,7 +17,8 @@ achieved FLOP/s = 2 x slots / time.
 
 Bytes per node update (algorithmic, one read and one write of every plane):
 FP32 form 42*4*2 + 4*4 (moments written) + 2 + 2 (lattice codes) + 8*4*2
-(multipliers of the warm start) = 420 B; FP64 plain 42*8*2 + 4*8 + 4 = 708 B.
+(multipliers of the warm start) = 420 B; FP64 plain 42*8*2 + 4*8 + 4 + 8*8*2
+= 836 B.
 """
 from __future__ import annotations
 
@@ -34,7 +35,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # measured again whenever a kernel changes (see profiles/).
 CALIBRATION = {"fp32": 1143.8 / 1244.2, "fp64": 1.0}
 
-BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2, "fp64": 42 * 8 * 2 + 4 * 8 + 4}
+BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
+                  "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}
 
 _XI = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1),
        (2, 0), (0, 2), (-2, 0), (0, -2), (2, 2), (-2, 2), (-2, -2), (2, -2),

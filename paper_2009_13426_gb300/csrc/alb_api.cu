@@ -106,8 +106,15 @@ int alb_config_default(alb_config* c) {
   c->sensor_alpha[2] = 1.6;
   c->newton_tol = 1e-12;
   c->newton_maxit = 50;
+  c->newton_start = ALB_START_AUTO;
   c->stream = nullptr;
   return ALB_OK;
+}
+
+// Whether the solves of this configuration start from the stored multipliers.
+static bool uses_previous_start(const alb_config* c) {
+  return c->newton_start == ALB_START_PREVIOUS ||
+         (c->newton_start == ALB_START_AUTO && c->precision == ALB_FP32_FORM);
 }
 
 static int check_config(const alb_config* c) {
@@ -130,6 +137,9 @@ static int check_config(const alb_config* c) {
     return fail(ALB_EINVAL, "sensor_eps must be positive and increasing");
   if (!(c->newton_tol > 0.0) || c->newton_maxit < 1)
     return fail(ALB_EINVAL, "newton_tol must be > 0 and newton_maxit >= 1");
+  if (c->newton_start != ALB_START_AUTO && c->newton_start != ALB_START_MAXWELLIAN &&
+      c->newton_start != ALB_START_PREVIOUS)
+    return fail(ALB_EINVAL, "unknown newton_start %d", c->newton_start);
   return ALB_OK;
 }
 
@@ -156,6 +166,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.bcy = cfg->bc_y;
   p.sensor = cfg->sensor;
   p.maxit = cfg->newton_maxit;
+  p.warm = uses_previous_start(cfg) ? 1 : 0;
   p.nu = cfg->nu;
   p.gamma = cfg->gamma;
   p.n0 = cfg->n0;
@@ -206,7 +217,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
     ALLOC(d.mom[b], 4 * d.ps * es);
     ALLOC(d.lat[b], d.ps);
     ALLOC(d.nxt[b], d.ps);
-    if (d.precision == ALB_FP32_FORM) ALLOC(d.lam[b], NM * d.ps * sizeof(float));
+    if (p.warm) ALLOC(d.lam[b], NM * d.ps * es);
   }
   ALLOC(d.ctr, CTR_COUNT * sizeof(unsigned long long));
   ALLOC(h->staging, 4 * d.n * sizeof(double));
@@ -415,7 +426,7 @@ size_t flow_device_bytes(const alb_config* c) {
   const size_t n = (size_t)c->nx * c->ny, ps = (n + 63) / 64 * 64;
   const size_t es = c->precision == ALB_FP64_PLAIN ? sizeof(double) : sizeof(float);
   size_t b = 2 * (NPLANES * ps * es + 4 * ps * es + 2 * ps);
-  if (c->precision == ALB_FP32_FORM) b += 2 * NM * ps * sizeof(float);
+  if (uses_previous_start(c)) b += 2 * NM * ps * es;
   b += CTR_COUNT * sizeof(unsigned long long) + 4 * n * sizeof(double) +
        (size_t)(totals_blocks((long long)n) + 1) * 4 * sizeof(double) + 4 * sizeof(double);
   return b;

@@ -49,6 +49,7 @@ struct Params {
   int bcx, bcy;      // 0 periodic, 1 zero-gradient
   int sensor;
   int maxit;
+  int warm;          // 1: solves start from the previous step's multipliers
   double nu, gamma, n0, tol;
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
   double seps[3], salpha[3];
@@ -160,20 +161,34 @@ __device__ __forceinline__ void maxwellian_guess(double ubx, double uby, double 
 // App. C), damped by backtracking on the strictly convex dual
 // F(lambda) = sum_i p_i + lambda . m, whose gradient is -G/rho and Hessian the
 // exact Jacobian sum_i p_i P P^T. Stops at max_k |G_k|/rho <= tol. On return p
-// holds the equilibrium per unit density at lam.
+// holds the equilibrium per unit density at lam. Starts from `warm` if given
+// (the node's multipliers of the previous step, moved to this lattice) and
+// from the Maxwellian if warm is null or gives a non-finite dual; the root is
+// unique, so the start changes only the path and round-off.
 // *iters counts Newton steps, *evals evaluations of the 21 exponentials.
 static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T, double tol,
                                                int maxit, double lam[NM], double p[Q], int* iters,
-                                               int* evals) {
+                                               int* evals, const double* warm = nullptr) {
   *iters = 0;
   *evals = 0;
   if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
   double m[NM];
   targets(ubx, uby, T, m);
-  maxwellian_guess(ubx, uby, T, lam);
-  exp_family(lam, p);
-  int ev = 2;
-  double F = dual_value(lam, p, m);
+  int ev = 0;
+  double F = 0.0;
+  if (warm) {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = warm[k];
+    exp_family(lam, p);
+    ev = 1;
+    F = dual_value(lam, p, m);
+  }
+  if (!warm || !isfinite(F)) {
+    maxwellian_guess(ubx, uby, T, lam);
+    exp_family(lam, p);
+    ev += 2;
+    F = dual_value(lam, p, m);
+  }
   int it = 0;
   for (;;) {
     double G[NM];

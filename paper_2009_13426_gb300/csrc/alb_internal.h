@@ -34,7 +34,7 @@ struct FlowDev {
   void* mom[2];      // 4 planes (rho, ux, uy, T) of double or float
   uint8_t* lat[2];   // lattice code of the stored populations
   uint8_t* nxt[2];   // lattice code selected for the next pull
-  float* lam[2];     // FP32 form: 8 planes of multipliers (warm start); else null
+  void* lam[2];      // 8 planes of multipliers in the population precision (warm start)
   unsigned long long* ctr;
   int cur;           // buffer holding the current state
 };
@@ -50,8 +50,8 @@ struct StepArgs {
   const uint8_t* nxt_in;
   uint8_t* lat_out;
   uint8_t* nxt_out;
-  const float* lam_in;  // FP32 form: multipliers of the previous step (8 planes)
-  float* lam_out;
+  const P* lam_in;  // multipliers of the previous step (8 planes)
+  P* lam_out;
   size_t ps;
   Params prm;
   unsigned long long* ctr;
@@ -61,7 +61,8 @@ template <typename P>
 inline StepArgs<P> step_args(const FlowDev& f, int in) {
   const int out = in ^ 1;
   return StepArgs<P>{(const P*)f.pop[in], (P*)f.pop[out], (const P*)f.mom[in], (P*)f.mom[out],
-                     f.lat[in], f.nxt[in], f.lat[out], f.nxt[out], f.lam[in], f.lam[out],
+                     f.lat[in], f.nxt[in], f.lat[out], f.nxt[out], (const P*)f.lam[in],
+                     (P*)f.lam[out],
                      f.ps, f.prm, f.ctr};
 }
 

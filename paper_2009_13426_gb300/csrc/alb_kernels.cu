@@ -40,7 +40,7 @@ struct InitArgs {
   P* mom_out;
   uint8_t* lat_out;
   uint8_t* nxt_out;
-  float* lam_out;
+  P* lam_out;
   size_t ps;
   Params prm;
   unsigned long long* ctr;
@@ -112,15 +112,13 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
       cl.pop[(Q + i) * BLOCK] = (P)(gfac * feq * (1.0 + phg));
     }
     if (ns == NEWTON_OK) {
-      float wbuf[NM];
-      const float* warm = nullptr;
-      if constexpr (std::is_same<P, float>::value) {
+      // the first collision starts from the multipliers just found if the
+      // flow starts its solves from previous multipliers
+      P wbuf[NM];
 #pragma unroll
-        for (int j = 0; j < NM; ++j) wbuf[j] = (float)lam[j];
-        warm = wbuf;
-      }
+      for (int j = 0; j < NM; ++j) wbuf[j] = (P)lam[j];
       collide_store<P, BLOCK>(pr, cl, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out,
-                              s_tab, warm, a.lam_out, &cnt, &n_fail);
+                              s_tab, pr.warm ? wbuf : nullptr, a.lam_out, &cnt, &n_fail);
     } else {
       for (int i = 0; i < NPLANES; ++i) a.pop_out[i * a.ps + k] = (P)0;
       a.mom_out[k] = (P)r;
@@ -129,9 +127,9 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
       a.mom_out[3 * a.ps + k] = (P)T;
       a.lat_out[k] = (uint8_t)code;
       a.nxt_out[k] = (uint8_t)code;
-      if constexpr (std::is_same<P, float>::value)
+      if (a.lam_out)
 #pragma unroll
-        for (int j = 0; j < NM; ++j) a.lam_out[j * a.ps + k] = j == 3 || j == 5 ? 0.5f : 0.0f;
+        for (int j = 0; j < NM; ++j) a.lam_out[j * a.ps + k] = j == 3 || j == 5 ? (P)0.5 : (P)0;
     }
   }
   warp_count(a.ctr + CTR_UNREALIZABLE, n_bad);
@@ -222,12 +220,12 @@ cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, cons
   cudaError_t e;
   if (f.precision == 0) {
     InitArgs<double> a{rho, rhoux, rhouy, rhoE, (double*)f.pop[out], (double*)f.mom[out],
-                       f.lat[out], f.nxt[out], nullptr, f.ps, f.prm, f.ctr};
+                       f.lat[out], f.nxt[out], (double*)f.lam[out], f.ps, f.prm, f.ctr};
     if ((e = allow_smem(init_kernel<double>, smem_bytes<double>())) != cudaSuccess) return e;
     init_kernel<double><<<grid_of(f.prm), BLOCK, smem_bytes<double>(), s>>>(a);
   } else {
     InitArgs<float> a{rho, rhoux, rhouy, rhoE, (float*)f.pop[out], (float*)f.mom[out],
-                      f.lat[out], f.nxt[out], f.lam[out], f.ps, f.prm, f.ctr};
+                      f.lat[out], f.nxt[out], (float*)f.lam[out], f.ps, f.prm, f.ctr};
     if ((e = allow_smem(init_kernel<float>, smem_bytes<float>())) != cudaSuccess) return e;
     init_kernel<float><<<grid_of(f.prm), BLOCK, smem_bytes<float>(), s>>>(a);
   }

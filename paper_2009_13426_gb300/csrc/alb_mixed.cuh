@@ -265,18 +265,18 @@ __device__ __forceinline__ void solve32(const Fact32& fc, const float g[NM], flo
 // every velocity u, where d = U - U' (a velocity xi relative to lattice U is
 // xi - d relative to U'). Exact for the exponential; it serves as the starting
 // point of the Newton iteration after a change of lattice.
-__device__ __forceinline__ void shift_multipliers(const float l[NM], float dx, float dy,
-                                                  float o[NM]) {
-  const float d2 = dx * dx + dy * dy;
+template <typename R>
+__device__ __forceinline__ void shift_multipliers(const R l[NM], R dx, R dy, R o[NM]) {
+  const R d2 = dx * dx + dy * dy;
   o[0] = l[0] - l[1] * dx - l[2] * dy + l[3] * dx * dx + l[4] * dx * dy + l[5] * dy * dy -
          l[6] * dx * d2 - l[7] * dy * d2;
-  o[1] = l[1] - 2.0f * l[3] * dx - l[4] * dy + l[6] * (3.0f * dx * dx + dy * dy) +
-         2.0f * l[7] * dx * dy;
-  o[2] = l[2] - l[4] * dx - 2.0f * l[5] * dy + 2.0f * l[6] * dx * dy +
-         l[7] * (dx * dx + 3.0f * dy * dy);
-  o[3] = l[3] - 3.0f * l[6] * dx - l[7] * dy;
-  o[4] = l[4] - 2.0f * l[6] * dy - 2.0f * l[7] * dx;
-  o[5] = l[5] - l[6] * dx - 3.0f * l[7] * dy;
+  o[1] = l[1] - (R)2 * l[3] * dx - l[4] * dy + l[6] * ((R)3 * dx * dx + dy * dy) +
+         (R)2 * l[7] * dx * dy;
+  o[2] = l[2] - l[4] * dx - (R)2 * l[5] * dy + (R)2 * l[6] * dx * dy +
+         l[7] * (dx * dx + (R)3 * dy * dy);
+  o[3] = l[3] - (R)3 * l[6] * dx - l[7] * dy;
+  o[4] = l[4] - (R)2 * l[6] * dy - (R)2 * l[7] * dx;
+  o[5] = l[5] - l[6] * dx - (R)3 * l[7] * dy;
   o[6] = l[6];
   o[7] = l[7];
 }

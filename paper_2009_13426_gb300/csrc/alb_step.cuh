@@ -34,20 +34,27 @@ struct Columns {
 };
 
 // Equilibrium of one node in the storage precision P: the full FP64 Newton for
-// the FP64 plain path, the mixed FP32/FP64 solver for the FP32 form. The
+// the FP64 plain path, the mixed FP32/FP64 solver for the FP32 form, both
+// started from `warm` (multipliers in precision P) when given. The
 // equilibrium per unit density lands in eq[i * B].
 template <typename P, int B = BLOCK>
 __device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, double uby,
-                                                double T, const double* tab, const float* warm,
+                                                double T, const double* tab, const P* warm,
                                                 double* eq, double lam[NM], SolveCount* cnt) {
   if constexpr (std::is_same<P, float>::value) {
     return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, eq, B, lam, cnt);
   } else {
     int it = 0, ev = 0;
     double p[Q];
-    const int st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev);
+    int st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev, warm);
     cnt->fp64_iters += it;
     cnt->fp64_evals += ev;
+    if (warm && st != NEWTON_OK && st != NEWTON_UNREALIZABLE) {
+      // the previous multipliers led nowhere: start again from the Maxwellian
+      st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev, nullptr);
+      cnt->fp64_iters += it;
+      cnt->fp64_evals += ev;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) eq[i * B] = p[i];
     return st;
@@ -76,11 +83,12 @@ struct Acc<float> {
   __device__ __forceinline__ float valf() const { return s + c; }
 };
 
-// Multipliers stored for node k (8 planes), moved into the frame of lattice
-// (Ux, Uy) from the lattice code they were computed in.
-__device__ __forceinline__ void load_warm(const float* lam, size_t ps, size_t k, int code_from,
-                                          int Ux, int Uy, float w[NM]) {
-  float l[NM];
+// Multipliers stored for node k (8 planes of L), moved into the frame of
+// lattice (Ux, Uy) from the lattice code they were computed in.
+template <typename L>
+__device__ __forceinline__ void load_warm(const L* lam, size_t ps, size_t k, int code_from,
+                                          int Ux, int Uy, L w[NM]) {
+  L l[NM];
 #pragma unroll
   for (int j = 0; j < NM; ++j) l[j] = lam[j * ps + k];
   const int dx = lat_ux(code_from) - Ux, dy = lat_uy(code_from) - Uy;
@@ -88,7 +96,7 @@ __device__ __forceinline__ void load_warm(const float* lam, size_t ps, size_t k,
 #pragma unroll
     for (int j = 0; j < NM; ++j) w[j] = l[j];
   } else {
-    shift_multipliers(l, (float)dx, (float)dy, w);
+    shift_multipliers<L>(l, (L)dx, (L)dy, w);
   }
 }
 
@@ -103,7 +111,7 @@ template <typename P, int B>
 __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
                                          int i, int cx, int cy, int Upx, int Upy, int sx, int sy,
                                          double* fi, double* gi, const double* tab, double* eq,
-                                         const float* lam_in, const uint8_t* lat_in,
+                                         const P* lam_in, const uint8_t* lat_in,
                                          SolveCount* cnt) {
   bool gh = false;
   const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
@@ -130,10 +138,10 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
   const double ubx = ux - Upx, uby = uy - Upy;
   double lam[NM];
-  float wbuf[NM];
-  const float* warm = nullptr;
-  if constexpr (std::is_same<P, float>::value) {
-    load_warm(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
+  P wbuf[NM];
+  const P* warm = nullptr;
+  if (pr.warm) {
+    load_warm<P>(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
     warm = wbuf;
   }
   const int st = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, eq, lam, cnt)
@@ -168,7 +176,7 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
                                               size_t k, size_t ps, P* __restrict__ pop_out,
                                               P* __restrict__ mom_out, uint8_t* lat_out,
                                               uint8_t* nxt_out, const double* tab,
-                                              const float* warm, float* lam_out,
+                                              const P* warm, P* lam_out,
                                               SolveCount* cnt, unsigned* n_fail) {
   const P* st = cl.pop;
   const int Ux = lat_ux(code), Uy = lat_uy(code);
@@ -197,17 +205,17 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   double lam[NM];
   const int ns = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, cl.eq, lam, cnt)
                              : NEWTON_UNREALIZABLE;
-  if constexpr (std::is_same<P, float>::value) {
-    // multipliers for the next step's warm start (lattice `code`)
+  // multipliers for the next step's warm start (lattice `code`), if stored
+  if (lam_out) {
     if (ns == NEWTON_OK) {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = (float)lam[j];
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = (P)lam[j];
     } else if (warm) {
 #pragma unroll
       for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = warm[j];
     } else {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = j == 3 || j == 5 ? 0.5f : 0.0f;
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = j == 3 || j == 5 ? (P)0.5 : (P)0;
     }
   }
   if (ns == NEWTON_OK) {
@@ -307,10 +315,10 @@ __device__ __forceinline__ void node_step(const StepArgs<P>& a, int x, int y,
     cl.pop[i * B] = (P)fd;
     cl.pop[(Q + i) * B] = (P)gd;
   }
-  float wbuf[NM];
-  const float* warm = nullptr;
-  if constexpr (std::is_same<P, float>::value) {
-    load_warm(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
+  P wbuf[NM];
+  const P* warm = nullptr;
+  if (pr.warm) {
+    load_warm<P>(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
     warm = wbuf;
   }
   collide_store<P, B>(pr, cl, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,

@@ -50,9 +50,10 @@ def run_replay(alb, nx, ny, fields, steps, precision, **kw):
     Feeding the oracle the same decisions isolates the arithmetic; the decisions
     themselves are checked bit-exactly on identical moments elsewhere."""
     fl = run_gpu(alb, nx, ny, fields, 0, precision, **kw)
-    s = O.Simulation(O.make_config(nx, ny, **kw))
+    okw = {k: v for k, v in kw.items() if k != "newton_start"}  # GPU-only option
+    s = O.Simulation(O.make_config(nx, ny, **okw))
     assert s.init(*fields) == O.OK
-    free = O.Simulation(O.make_config(nx, ny, **kw))
+    free = O.Simulation(O.make_config(nx, ny, **okw))
     assert free.init(*fields) == O.OK
     differs = 0
     for _ in range(steps):
@@ -155,6 +156,29 @@ def test_vortex_fp64_plain_matches_oracle(alb, vortex_oracle):
     st = fl.stats()
     assert st["newton_failures"] == 0 and st["reconstruction_failures"] == 0
     assert st["reconstructions"] == ostats["reconstructions"]
+
+
+def test_vortex_fp64_previous_start_matches_oracle(alb, vortex_oracle):
+    """FP64 plain with every solve started from the previous step's
+    multipliers (ALB_START_PREVIOUS): a different Newton path to the same
+    unique root, fewer iterations, the same 1e-11 on the vortex."""
+    fields, ref, (rx, ry), ostats = vortex_oracle
+    cold = run_gpu(alb, 64, 64, fields, 100, alb.ALB_FP64_PLAIN, umax=2, nu=1e-3)
+    fl = run_gpu(alb, 64, 64, fields, 100, alb.ALB_FP64_PLAIN, umax=2, nu=1e-3,
+                 newton_start=alb.ALB_START_PREVIOUS)
+    err = rel_errors(fl.moments(), ref)
+    assert max(err.values()) <= FP64_TOL, err
+    sx, sy = fl.shifts()
+    assert (sx == rx).all() and (sy == ry).all()
+    assert fl.stats()["newton_iterations"] < 0.7 * cold.stats()["newton_iterations"]
+
+
+def test_vortex_fp32_maxwellian_start_matches_oracle(alb, vortex_oracle):
+    fields = vortex_oracle[0]
+    fl, s, _ = run_replay(alb, 64, 64, fields, 20, alb.ALB_FP32_FORM, umax=2, nu=1e-3,
+                          newton_start=alb.ALB_START_MAXWELLIAN)
+    err = rel_errors(fl.moments(), s.moments())
+    assert max(err.values()) <= FP32_TOL, err
 
 
 def test_vortex_fp32_form_matches_oracle(alb, vortex_oracle):
