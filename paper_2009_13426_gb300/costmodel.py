@@ -58,28 +58,47 @@ def _nnz2(a, b):
 
 # ---------------------------------------------------------------- FP64 plain
 
+# The groups of the D2Q21 set: the rest velocity, six symmetric axis pairs
+# (point indices), two diagonal quadruples.
+_PAIRS = [(1, 3), (2, 4), (9, 11), (10, 12), (17, 19), (18, 20)]
+_QUADS = [(5, 6, 7, 8), (13, 14, 15, 16)]
+
+
+def _pm(k, i):
+    return _mono(k, *_XI[i])
+
+
 def plain_eval():
-    """21 exponents (1 + lambda_0 plus the non-zero monomials), 21 CUDA exp,
-    and the dual value (21 adds + 8 FMA)."""
-    ops = sum(1 + sum(1 for k in range(1, 8) if _mono(k, x, y) != 0) for x, y in _XI)
-    return ops + 21 * W_EXP + 21 + 8
+    """Grouped exponents (55), 21 table-driven exponentials (9 each), grouped
+    constraint sums incl. sum p (68), dual value lambda . m (8)."""
+    return 55 + 21 * 9 + 68 + 8
+
+
+def plain_jacobian():
+    """Jacobian from the groups: one FMA per non-zero coefficient and group,
+    plus the pair sums/differences and the quadruple butterflies."""
+    n = 0
+    for ip, _ in _PAIRS:
+        n += 2 + sum(1 for a in range(8) for b in range(a + 1) if _pm(a, ip) * _pm(b, ip) != 0)
+    for q in _QUADS:
+        n += 8 + sum(1 for a in range(8) for b in range(a + 1) if _pm(a, q[0]) * _pm(b, q[0]) != 0)
+    return n
 
 
 def plain_newton_step():
-    """Residual, Jacobian, Cholesky, two triangular solves, step, line-search
+    """Residual and its maximum, grouped Jacobian, Cholesky with reciprocal
+    pivots, two triangular solves by multiplication, step and line-search
     bookkeeping (the line-search evaluation itself is an eval)."""
-    g = sum(_nnz(k) for k in range(8)) + 8
-    h = sum(_nnz2(a, b) for a in range(8) for b in range(a + 1))
-    chol = 0.0
-    for j in range(8):
-        chol += j + 1 + W_SQRT + W_DIV + sum(j + 1 for _ in range(j + 1, 8))
-    solves = 2 * (28 + 8 * W_DIV)
-    return g + h + chol + solves + 8 + 8 + 4
+    g = 8 + 8
+    chol = sum(j + W_SQRT + W_DIV + (7 - j) * (j + 1) for j in range(8))
+    solves = 2 * (28 + 8)
+    return g + plain_jacobian() + chol + solves + 8 + 8 + 4
 
 
 def plain_call():
-    """Targets, Maxwellian guess (reciprocal, normalisation, log)."""
-    return 8 + W_DIV + 4 + 21 + W_LOG
+    """Targets, Maxwellian start (reciprocal of T, log and reciprocal of the
+    normalisation, scaling of the 21 populations and 8 sums)."""
+    return 8 + W_DIV + 4 + W_LOG + W_DIV + 21 + 8
 
 
 # ---------------------------------------------------------------- FP32 form

@@ -128,16 +128,6 @@ __device__ __forceinline__ void exp_family(const double lam[NM], double p[Q]) {
   }
 }
 
-__device__ __forceinline__ double dual_value(const double lam[NM], const double p[Q],
-                                             const double m[NM]) {
-  double F = 0.0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) F += p[i];
-#pragma unroll
-  for (int k = 0; k < NM; ++k) F = fma(lam[k], m[k], F);
-  return F;
-}
-
 enum { NEWTON_OK = 0, NEWTON_MAXIT = 1, NEWTON_SINGULAR = 2, NEWTON_UNREALIZABLE = 3 };
 
 // Maxwellian starting multipliers, lambda_0 from the normalisation sum p = 1.
@@ -155,123 +145,6 @@ __device__ __forceinline__ void maxwellian_guess(double ubx, double uby, double 
 #pragma unroll
   for (int i = 0; i < Q; ++i) Z += p[i];
   lam[0] = log(Z);
-}
-
-// FP64 Newton on the multipliers of the 8-moment equilibrium (Sec. II.C.2,
-// App. C), damped by backtracking on the strictly convex dual
-// F(lambda) = sum_i p_i + lambda . m, whose gradient is -G/rho and Hessian the
-// exact Jacobian sum_i p_i P P^T. Stops at max_k |G_k|/rho <= tol. On return p
-// holds the equilibrium per unit density at lam. Starts from `warm` if given
-// (the node's multipliers of the previous step, moved to this lattice) and
-// from the Maxwellian if warm is null or gives a non-finite dual; the root is
-// unique, so the start changes only the path and round-off.
-// *iters counts Newton steps, *evals evaluations of the 21 exponentials.
-static __device__ __noinline__ int newton_fp64(double ubx, double uby, double T, double tol,
-                                               int maxit, double lam[NM], double p[Q], int* iters,
-                                               int* evals, const double* warm = nullptr) {
-  *iters = 0;
-  *evals = 0;
-  if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
-  double m[NM];
-  targets(ubx, uby, T, m);
-  int ev = 0;
-  double F = 0.0;
-  if (warm) {
-#pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] = warm[k];
-    exp_family(lam, p);
-    ev = 1;
-    F = dual_value(lam, p, m);
-  }
-  if (!warm || !isfinite(F)) {
-    maxwellian_guess(ubx, uby, T, lam);
-    exp_family(lam, p);
-    ev += 2;
-    F = dual_value(lam, p, m);
-  }
-  int it = 0;
-  for (;;) {
-    double G[NM];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) {
-      double s = -m[k];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) s = madd(s, p[i], PM(k, i));
-      G[k] = s;
-    }
-    double gmax = 0.0;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) gmax = fmax(gmax, fabs(G[k]));
-    if (!isfinite(gmax)) { *iters = it; *evals = ev; return NEWTON_SINGULAR; }
-    if (gmax <= tol) { *iters = it; *evals = ev; return NEWTON_OK; }
-    if (it >= maxit) { *iters = it; *evals = ev; return NEWTON_MAXIT; }
-    // Jacobian (lower triangle), then in-place Cholesky factor
-    double H[NM][NM];
-#pragma unroll
-    for (int a = 0; a < NM; ++a)
-#pragma unroll
-      for (int b = 0; b <= a; ++b) {
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) s = madd(s, p[i], PM(a, i) * PM(b, i));
-        H[a][b] = s;
-      }
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < NM; ++j) {
-      double d = H[j][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) d = fma(-H[j][k], H[j][k], d);
-      ok = ok && (d > 0.0);
-      const double l = sqrt(fmax(d, 1e-300));
-      const double il = 1.0 / l;
-      H[j][j] = l;
-#pragma unroll
-      for (int i = j + 1; i < NM; ++i) {
-        double s = H[i][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) s = fma(-H[i][k], H[j][k], s);
-        H[i][j] = s * il;
-      }
-    }
-    if (!ok) { *iters = it; *evals = ev; return NEWTON_SINGULAR; }
-    double d[NM];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) {
-      double s = G[i];
-#pragma unroll
-      for (int k = 0; k < i; ++k) s = fma(-H[i][k], d[k], s);
-      d[i] = s / H[i][i];
-    }
-#pragma unroll
-    for (int i = NM - 1; i >= 0; --i) {
-      double s = d[i];
-#pragma unroll
-      for (int k = i + 1; k < NM; ++k) s = fma(-H[k][i], d[k], s);
-      d[i] = s / H[i][i];
-    }
-    double gd = 0.0;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) gd = fma(G[k], d[k], gd);
-    // backtracking (Armijo) along lam + t d
-    double t = 1.0, Fc = 0.0;
-    bool accepted = false;
-    double lc[NM];
-    for (int ls = 0; ls < 40; ++ls) {
-#pragma unroll
-      for (int k = 0; k < NM; ++k) lc[k] = fma(t, d[k], lam[k]);
-      exp_family(lc, p);
-      ++ev;
-      Fc = dual_value(lc, p, m);
-      if (isfinite(Fc) && Fc <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = true; break; }
-      t *= 0.5;
-    }
-    ++it;
-    if (!accepted) { exp_family(lam, p); *iters = it; *evals = ev + 1; return NEWTON_MAXIT; }
-#pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] = lc[k];
-    F = Fc;
-  }
 }
 
 // exp(-(1 + lambda . P(xi_i))) for one velocity given at run time.

@@ -423,6 +423,201 @@ struct SolveCount {
   unsigned fp32_iters = 0, fp64_evals = 0, fp64_iters = 0;
 };
 
+// Jacobian H = sum_i p_i P(xi_i) P(xi_i)^T (packed lower triangle) from the
+// populations per unit density in col[i * stride], group by group: a
+// symmetric pair contributes its sum or difference, a diagonal quadruple one
+// of its four parity combinations, with the compile-time value of P_a P_b at
+// the group's first point as coefficient.
+template <int IP, int IM>
+__device__ __forceinline__ void jac_pair(const double* col, int stride, double H[36]) {
+  const double pp = col[IP * stride], pm = col[IM * stride];
+  const double S = pp + pm, D = pp - pm;
+#pragma unroll
+  for (int a = 0; a < NM; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const int c = PM(a, IP) * PM(b, IP);
+      if (c != 0) H[tri(a, b)] = madd(H[tri(a, b)], PM(a, IM) * PM(b, IM) == c ? S : D, c);
+    }
+}
+
+template <int IPP, int IMP, int IMM, int IPM>
+__device__ __forceinline__ void jac_quad(const double* col, int stride, double H[36]) {
+  const double ppp = col[IPP * stride], pmp = col[IMP * stride];
+  const double pmm = col[IMM * stride], ppm = col[IPM * stride];
+  const double Ap = ppp + ppm, Bm = pmp + pmm, Cp = ppp - ppm, Dm = pmp - pmm;
+  const double ee = Ap + Bm, oe = Ap - Bm, eo = Cp + Dm, oo = Cp - Dm;
+#pragma unroll
+  for (int a = 0; a < NM; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const int c = PM(a, IPP) * PM(b, IPP);
+      const bool xodd = PM(a, IMP) * PM(b, IMP) == -c;  // x -> -x flips the sign
+      const bool yodd = PM(a, IPM) * PM(b, IPM) == -c;  // y -> -y flips the sign
+      if (c != 0)
+        H[tri(a, b)] = madd(H[tri(a, b)], xodd ? (yodd ? oo : oe) : (yodd ? eo : ee), c);
+    }
+}
+
+__device__ __forceinline__ void jacobian_grouped(const double* col, int stride, double H[36]) {
+#pragma unroll
+  for (int k = 0; k < 36; ++k) H[k] = 0.0;
+  H[0] = col[0];  // rest velocity: only P_0 = 1 is non-zero
+  jac_pair<1, 3>(col, stride, H);
+  jac_pair<2, 4>(col, stride, H);
+  jac_pair<9, 11>(col, stride, H);
+  jac_pair<10, 12>(col, stride, H);
+  jac_pair<17, 19>(col, stride, H);
+  jac_pair<18, 20>(col, stride, H);
+  jac_quad<5, 6, 7, 8>(col, stride, H);
+  jac_quad<13, 14, 15, 16>(col, stride, H);
+}
+
+// Evaluation of the exponential family at l: p_i = exp(-(1 + l . P(xi_i)))
+// into col, and the moments M_k = sum_i p_i P_k(xi_i) (table-driven FP64
+// exponential, grouped exponents and sums).
+__device__ __forceinline__ void eval_fp64(const double l[NM], const double* tab, double* col,
+                                          int stride, double M[NM]) {
+  PassG64 pg(tab, col, stride);
+  visit_groups<double>(l, pg);
+#pragma unroll
+  for (int k = 0; k < NM; ++k) M[k] = pg.M[k];
+}
+
+// FP64 Newton on the multipliers of the 8-moment equilibrium (Sec. II.C.2,
+// App. C): damped by backtracking (Armijo) on the strictly convex dual
+// F(lambda) = sum_i p_i + lambda . m, whose gradient is -G/rho and Hessian the
+// exact Jacobian sum_i p_i P P^T; stops at max_k |G_k|/rho <= tol. Starts from
+// `warm` if given, else (or if warm gives a non-finite dual) from the
+// Maxwellian with lambda_0 from the normalisation. The iteration is the
+// oracle's; its arithmetic is grouped by the symmetry of the velocity set and
+// uses the table-driven exponential. On return col[i * stride] holds the
+// equilibrium per unit density at lam; *iters counts Newton steps, *evals
+// evaluations of the 21 exponentials.
+static __device__ __noinline__ int newton_fp64g(double ubx, double uby, double T, double tol,
+                                                int maxit, const double* tab, double* col,
+                                                int stride, double lam[NM], int* iters,
+                                                int* evals, const double* warm) {
+  *iters = 0;
+  *evals = 0;
+  if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
+  double m[NM];
+  targets(ubx, uby, T, m);
+  double M[NM];
+  int ev = 0;
+  double F = 0.0;
+  if (warm) {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = warm[k];
+    eval_fp64(lam, tab, col, stride, M);
+    ev = 1;
+    F = M[0];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) F = fma(lam[k], m[k], F);
+  }
+  if (!warm || !isfinite(F)) {
+    // Maxwellian: lambda_1 = -u/T, lambda_xx = lambda_yy = 1/(2T), lambda_0
+    // from sum p = 1 (the exponentials at lambda_0 = 0 divided by their sum)
+    const double iT = 1.0 / T;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = 0.0;
+    lam[1] = -ubx * iT;
+    lam[2] = -uby * iT;
+    lam[3] = 0.5 * iT;
+    lam[5] = 0.5 * iT;
+    eval_fp64(lam, tab, col, stride, M);
+    ev += 1;
+    const double Z = M[0];
+    lam[0] = log(Z);
+    const double iZ = 1.0 / Z;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) col[i * stride] *= iZ;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) M[k] *= iZ;
+    F = M[0];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) F = fma(lam[k], m[k], F);
+  }
+  int it = 0;
+  for (;;) {
+    double G[NM];
+    double gmax = 0.0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      G[k] = M[k] - m[k];
+      gmax = fmax(gmax, fabs(G[k]));
+    }
+    if (!isfinite(gmax)) { *iters = it; *evals = ev; return NEWTON_SINGULAR; }
+    if (gmax <= tol) { *iters = it; *evals = ev; return NEWTON_OK; }
+    if (it >= maxit) { *iters = it; *evals = ev; return NEWTON_MAXIT; }
+    // Jacobian, then its Cholesky factor in place (reciprocal pivots kept)
+    double H[36], il[NM];
+    jacobian_grouped(col, stride, H);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+      double d = H[tri(j, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d = fma(-H[tri(j, k)], H[tri(j, k)], d);
+      ok = ok && (d > 0.0);
+      const double l = sqrt(fmax(d, 1e-300));
+      il[j] = 1.0 / l;
+      H[tri(j, j)] = l;
+#pragma unroll
+      for (int i = j + 1; i < NM; ++i) {
+        double s = H[tri(i, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = fma(-H[tri(i, k)], H[tri(j, k)], s);
+        H[tri(i, j)] = s * il[j];
+      }
+    }
+    if (!ok) { *iters = it; *evals = ev; return NEWTON_SINGULAR; }
+    double d[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      double s = G[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fma(-H[tri(i, k)], d[k], s);
+      d[i] = s * il[i];
+    }
+#pragma unroll
+    for (int i = NM - 1; i >= 0; --i) {
+      double s = d[i];
+#pragma unroll
+      for (int k = i + 1; k < NM; ++k) s = fma(-H[tri(k, i)], d[k], s);
+      d[i] = s * il[i];
+    }
+    double gd = 0.0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) gd = fma(G[k], d[k], gd);
+    // backtracking (Armijo) along lam + t d
+    double t = 1.0, Fc = 0.0;
+    bool accepted = false;
+    double lc[NM];
+    for (int ls = 0; ls < 40; ++ls) {
+#pragma unroll
+      for (int k = 0; k < NM; ++k) lc[k] = fma(t, d[k], lam[k]);
+      eval_fp64(lc, tab, col, stride, M);
+      ++ev;
+      Fc = M[0];
+#pragma unroll
+      for (int k = 0; k < NM; ++k) Fc = fma(lc[k], m[k], Fc);
+      if (isfinite(Fc) && Fc <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = true; break; }
+      t *= 0.5;
+    }
+    ++it;
+    if (!accepted) {
+      eval_fp64(lam, tab, col, stride, M);
+      *iters = it;
+      *evals = ev + 1;
+      return NEWTON_MAXIT;
+    }
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = lc[k];
+    F = Fc;
+  }
+}
+
 // Equilibrium of the FP32 form: FP32 Newton (from the warm start if given,
 // else from the Maxwellian; again from the Maxwellian if the warm start
 // fails), FP64 refinement, full FP64 Newton as the last fallback. The FP64
@@ -451,13 +646,10 @@ __device__ __forceinline__ int equilibrium_mixed(double ubx, double uby, double 
     cnt->fp64_evals += ev;
   }
   if (st != NEWTON_OK) {
-    double p[Q];
     int it = 0;
-    st = newton_fp64(ubx, uby, T, tol, maxit, lam, p, &it, &ev);
+    st = newton_fp64g(ubx, uby, T, tol, maxit, tab, col, stride, lam, &it, &ev, nullptr);
     cnt->fp64_iters += it;
     cnt->fp64_evals += ev;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) col[i * stride] = p[i];
   }
   return st;
 }

@@ -45,18 +45,15 @@ __device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, do
     return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, eq, B, lam, cnt);
   } else {
     int it = 0, ev = 0;
-    double p[Q];
-    int st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev, warm);
+    int st = newton_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev, warm);
     cnt->fp64_iters += it;
     cnt->fp64_evals += ev;
     if (warm && st != NEWTON_OK && st != NEWTON_UNREALIZABLE) {
       // the previous multipliers led nowhere: start again from the Maxwellian
-      st = newton_fp64(ubx, uby, T, pr.tol, pr.maxit, lam, p, &it, &ev, nullptr);
+      st = newton_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev, nullptr);
       cnt->fp64_iters += it;
       cnt->fp64_evals += ev;
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) eq[i * B] = p[i];
     return st;
   }
 }
