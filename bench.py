@@ -50,6 +50,12 @@ if ROOT not in sys.path:
 from paper_2009_13426_gb300 import costmodel, flows  # noqa: E402
 
 METRIC = "adaptive D2Q21 MLUPS, FP32 form vs FP64 plain at stated error; serve p50/p99"
+# DRAM bytes (read + write) per node update of step_kernel<float>, from one
+# ncu capture of the 1024^2 case of the same flow (dram__bytes_read.sum +
+# dram__bytes_write.sum = 654.6 MB for 1,048,576 nodes); the traffic grows in
+# proportion to the nodes, so a 4096^2 launch moves 16,777,216 x this.
+# Measured on the current kernel (profiles/step_kernel_fp32_shear.md).
+TRAFFIC_BYTES_PER_NODE_FP32 = 624.2
 UNIT = "MLUPS"
 NU = 1e-5
 
@@ -67,6 +73,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--batched-flows", type=int, default=256,
+                    help="use the first N flows of the 256 (smaller profiling runs)")
+    ap.add_argument("--no-tune", action="store_true", help="batched: keep the default shape")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-drain", type=float, default=90.0,
@@ -236,7 +245,7 @@ def run_batched(args):
     import torch
     from paper_2009_13426_gb300 import alb
 
-    specs = flows.batched_flows(256)
+    specs = flows.batched_flows(256)[:args.batched_flows]
     nodes = sum(sp.nx * sp.ny for sp in specs)
     stream = torch.cuda.Stream()
     b = alb.Batch([dict(nx=sp.nx, ny=sp.ny, nu=sp.nu, precision=alb.ALB_FP32_FORM)
@@ -245,7 +254,8 @@ def run_batched(args):
         for sp, fl in zip(specs, b.flows):
             fl.init(*sp.fields())
         t = time.perf_counter()
-        b.tune(trials=2)
+        if not args.no_tune:
+            b.tune(trials=2)
         tune_s = time.perf_counter() - t
         tuning = b.tuning(alb.ALB_FP32_FORM)
         b.step(args.warmup)
@@ -458,8 +468,15 @@ def run_ours(args, world, rank, local):
                    np.sqrt((a - A) ** 2 + (b - B) ** 2).max() / np.sqrt(A ** 2 + B ** 2).max(),
                    np.abs(e - E).max() / np.abs(E).max())
         tot = max(abs(r.sum() - R.sum()) / R.sum(), abs(e.sum() - E.sum()) / E.sum())
+        slots64 = costmodel.fp64_slots(d64, "fp64")
         extra["fp64_plain"] = {"value": round(N * k64 / (ms64 * 1e-3) / 1e6, 2), "unit": UNIT,
-                               "steps": k64, "ms_per_step": round(ms64 / k64, 3)}
+                               "steps": k64, "ms_per_step": round(ms64 / k64, 3),
+                               "fp64_slots_per_node": round(slots64 / k64 / N, 1),
+                               "fp64_tflops": round(2.0 * slots64 / (ms64 * 1e-3) / 1e12, 4),
+                               "counters": {k: d64[k] for k in ("newton_iterations",
+                                                                 "newton_calls",
+                                                                 "fp64_evaluations",
+                                                                 "reconstructions")}}
         extra["error"] = {"fp32_form_vs_fp64_plain_l2_rel": float("%.3e" % l2),
                           "totals_rel": float("%.3e" % tot),
                           "max_rel": float("%.3e" % linf),
@@ -520,7 +537,10 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": round(achieved_tflops, 4),
                      "peak": round(costmodel.FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                      "frac": round(achieved_tflops / costmodel.FP64_PEAK_TFLOPS, 4),
-                     "traffic": None,
+                     "traffic": round(TRAFFIC_BYTES_PER_NODE_FP32 * N),
+                     "traffic_note": "ncu DRAM bytes per node on the 1024^2 case x nodes; "
+                                     "above the 420 algorithmic bytes: register spills that "
+                                     "leave L2",
                      "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "kernel": "step_kernel<float>",
                      "fp64_slots_per_node": round(slots / args.steps / N, 1),

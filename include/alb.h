@@ -162,6 +162,32 @@ int alb_moments(alb_handle* h, double* rho, double* rhoux, double* rhouy, double
 /* Lattice shift (U_x, U_y) of the current populations, one byte each per node. */
 int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where);
 
+/* Lattice shift selected for the next pull (Eq. criterion applied at the
+ * last collision), one byte each per node. */
+int alb_next_shifts(alb_handle* h, signed char* ux, signed char* uy, int where);
+
+/* Post-collision populations of the current state as FP64 planes:
+ * f[i * n + k], g[i * n + k] for velocity i (order of alb_velocities) and
+ * node k = y * nx + x, n = nx * ny; 21 planes each. They live in the lattice
+ * of alb_shifts. */
+int alb_populations(alb_handle* h, double* f, double* g, int where);
+
+/* Primitive moments stored with the current state (rho, u_x, u_y, T; the
+ * values the next step's rebuilds read), as FP64 arrays of n. */
+int alb_primitives(alb_handle* h, double* rho, double* ux, double* uy, double* T, int where);
+
+/* Checkpoint / restart. alb_checkpoint_size gives the bytes of an image of
+ * the whole flow state (populations, moments, lattices, stored multipliers,
+ * counters, step count, and a header naming the configuration);
+ * alb_checkpoint_save writes it to host memory buf (synchronises);
+ * alb_checkpoint_load restores it into a flow of the same grid, precision,
+ * start option, u_max and boundaries (ALB_EINVAL otherwise). Continuing
+ * from a loaded image gives the same results bit for bit as continuing
+ * the saved flow. The paper has no counterpart. */
+int alb_checkpoint_size(alb_handle* h, size_t* bytes);
+int alb_checkpoint_save(alb_handle* h, void* buf);
+int alb_checkpoint_load(alb_handle* h, const void* buf);
+
 /* Global totals of the current state: out[0..3] = sum over nodes of rho,
  * rho ux, rho uy, rho E (host memory, 4 doubles). Mass, momentum and total
  * energy are the invariants of the collision (Eqs. G0_8mom..G2yy_8mom with

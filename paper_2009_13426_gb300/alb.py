@@ -130,6 +130,13 @@ _SIGS = {
                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "alb_velocities": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "alb_next_shifts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int]),
+    "alb_populations": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int]),
+    "alb_primitives": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int]),
+    "alb_checkpoint_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "alb_checkpoint_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "alb_checkpoint_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "alb_batch_variants": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "alb_batch_create": (ctypes.c_int, [ctypes.POINTER(alb_config), ctypes.c_int, ctypes.c_void_p,
@@ -258,6 +265,33 @@ def alb_moments(h, out):
 
 def alb_shifts(h, ux, uy):
     return _check(lib().alb_shifts(h, _ptr(ux), _ptr(uy), _where(ux)))
+
+
+def alb_next_shifts(h, ux, uy):
+    return _check(lib().alb_next_shifts(h, _ptr(ux), _ptr(uy), _where(ux)))
+
+
+def alb_populations(h, f, g):
+    """f, g: 21 * nx * ny float64 each (plane i at [i * n, (i + 1) * n))."""
+    return _check(lib().alb_populations(h, _ptr(f), _ptr(g), _where(f)))
+
+
+def alb_primitives(h, out):
+    """out: 4 arrays (rho, ux, uy, T) of nx * ny float64."""
+    return _check(lib().alb_primitives(h, *[_ptr(a) for a in out], _where(out[0])))
+
+
+def alb_checkpoint_save(h) -> np.ndarray:
+    n = ctypes.c_size_t()
+    _check(lib().alb_checkpoint_size(h, ctypes.byref(n)))
+    buf = np.empty(n.value, np.uint8)
+    _check(lib().alb_checkpoint_save(h, buf.ctypes.data))
+    return buf
+
+
+def alb_checkpoint_load(h, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, np.uint8)
+    return _check(lib().alb_checkpoint_load(h, buf.ctypes.data))
 
 
 def alb_stats_get(h) -> dict:
@@ -403,6 +437,33 @@ class Flow:
         uy = np.empty(n, np.int8)
         alb_shifts(self.h, ux, uy)
         return ux.reshape(self.ny, self.nx), uy.reshape(self.ny, self.nx)
+
+    def next_shifts(self):
+        n = self.nx * self.ny
+        ux = np.empty(n, np.int8)
+        uy = np.empty(n, np.int8)
+        alb_next_shifts(self.h, ux, uy)
+        return ux.reshape(self.ny, self.nx), uy.reshape(self.ny, self.nx)
+
+    def populations(self):
+        """(f, g), each (21, ny, nx) float64: the post-collision populations."""
+        n = self.nx * self.ny
+        f = np.empty(21 * n)
+        g = np.empty(21 * n)
+        alb_populations(self.h, f, g)
+        return f.reshape(21, self.ny, self.nx), g.reshape(21, self.ny, self.nx)
+
+    def primitives(self):
+        n = self.nx * self.ny
+        out = [np.empty(n) for _ in range(4)]
+        alb_primitives(self.h, out)
+        return [a.reshape(self.ny, self.nx) for a in out]
+
+    def checkpoint(self):
+        return alb_checkpoint_save(self.h)
+
+    def restore(self, buf):
+        return alb_checkpoint_load(self.h, buf)
 
     def stats(self):
         return alb_stats_get(self.h)

@@ -340,6 +340,155 @@ int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where) {
   return ALB_OK;
 }
 
+int alb_next_shifts(alb_handle* h, signed char* ux, signed char* uy, int where) {
+  if (!h || !ux || !uy) return fail(ALB_EINVAL, "alb_next_shifts: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_next_shifts: call alb_init first");
+  const size_t n = h->dev.n;
+  if (where == ALB_DEVICE) {
+    ALB_CUDA(launch_export_shifts(h->dev, ux, uy, h->stream, true), "alb_next_shifts");
+    return ALB_OK;
+  }
+  if (where != ALB_HOST) return fail(ALB_EINVAL, "alb_next_shifts: bad where");
+  signed char* s = (signed char*)h->staging;
+  ALB_CUDA(launch_export_shifts(h->dev, s, s + n, h->stream, true), "alb_next_shifts");
+  ALB_CUDA(cudaMemcpyAsync(ux, s, n, cudaMemcpyDeviceToHost, h->stream), "alb_next_shifts: D2H");
+  ALB_CUDA(cudaMemcpyAsync(uy, s + n, n, cudaMemcpyDeviceToHost, h->stream),
+           "alb_next_shifts: D2H");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_next_shifts: synchronise");
+  return ALB_OK;
+}
+
+// Planes of the current buffer as FP64 planes: what = 0 populations (outs[0]
+// receives planes 0..20, outs[1] planes 21..41), what = 1 moments (outs[j]
+// receives plane j).
+static int export_planes(alb_handle* h, int what, double* const* outs, int nout, int per_out,
+                         int where, const char* name) {
+  const size_t n = h->dev.n;
+  if (where == ALB_DEVICE) {
+    for (int j = 0; j < nout; ++j)
+      ALB_CUDA(launch_export_planes(h->dev, what, j * per_out, per_out, outs[j], h->stream), name);
+    return ALB_OK;
+  }
+  if (where != ALB_HOST) return fail(ALB_EINVAL, "%s: bad where", name);
+  // through the staging buffer (4 planes of n doubles at a time)
+  double* st = h->staging;
+  for (int j = 0; j < nout; ++j)
+    for (int p = 0; p < per_out; p += 4) {
+      const int np = per_out - p < 4 ? per_out - p : 4;
+      ALB_CUDA(launch_export_planes(h->dev, what, j * per_out + p, np, st, h->stream), name);
+      ALB_CUDA(cudaMemcpyAsync(outs[j] + (size_t)p * n, st, (size_t)np * n * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream), name);
+      ALB_CUDA(cudaStreamSynchronize(h->stream), name);
+    }
+  return ALB_OK;
+}
+
+int alb_populations(alb_handle* h, double* f, double* g, int where) {
+  if (!h || !f || !g) return fail(ALB_EINVAL, "alb_populations: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_populations: call alb_init first");
+  double* outs[2] = {f, g};
+  return export_planes(h, 0, outs, 2, Q, where, "alb_populations");
+}
+
+int alb_primitives(alb_handle* h, double* rho, double* ux, double* uy, double* T, int where) {
+  if (!h || !rho || !ux || !uy || !T) return fail(ALB_EINVAL, "alb_primitives: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_primitives: call alb_init first");
+  double* outs[4] = {rho, ux, uy, T};
+  return export_planes(h, 1, outs, 4, 1, where, "alb_primitives");
+}
+
+// ------------------------------------------------------------- checkpoints
+
+struct CheckpointHeader {
+  char magic[8];          // "ALBCKPT1"
+  int32_t nx, ny, precision, warm;
+  int32_t u_max, bc_x, bc_y, reserved;
+  uint64_t ps, steps;
+};
+
+struct Piece {
+  void* dev;
+  size_t bytes;
+};
+
+static int checkpoint_pieces(alb_handle* h, Piece* out) {
+  const FlowDev& d = h->dev;
+  const size_t es = d.precision == ALB_FP64_PLAIN ? sizeof(double) : sizeof(float);
+  const int b = d.cur;
+  int k = 0;
+  out[k++] = {d.pop[b], NPLANES * d.ps * es};
+  out[k++] = {d.mom[b], 4 * d.ps * es};
+  out[k++] = {d.lat[b], d.ps};
+  out[k++] = {d.nxt[b], d.ps};
+  if (d.prm.warm) out[k++] = {d.lam[b], NM * d.ps * es};
+  out[k++] = {d.ctr, CTR_COUNT * sizeof(unsigned long long)};
+  return k;
+}
+
+int alb_checkpoint_size(alb_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(ALB_EINVAL, "alb_checkpoint_size: null pointer");
+  Piece pc[6];
+  const int k = checkpoint_pieces(h, pc);
+  size_t total = sizeof(CheckpointHeader);
+  for (int j = 0; j < k; ++j) total += pc[j].bytes;
+  *bytes = total;
+  return ALB_OK;
+}
+
+int alb_checkpoint_save(alb_handle* h, void* buf) {
+  if (!h || !buf) return fail(ALB_EINVAL, "alb_checkpoint_save: null pointer");
+  if (!h->initialised) return fail(ALB_EINVAL, "alb_checkpoint_save: call alb_init first");
+  CheckpointHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "ALBCKPT1", 8);
+  hd.nx = h->cfg.nx;
+  hd.ny = h->cfg.ny;
+  hd.precision = h->dev.precision;
+  hd.warm = h->dev.prm.warm;
+  hd.u_max = h->cfg.u_max;
+  hd.bc_x = h->cfg.bc_x;
+  hd.bc_y = h->cfg.bc_y;
+  hd.ps = h->dev.ps;
+  hd.steps = h->steps;
+  unsigned char* p = (unsigned char*)buf;
+  memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  Piece pc[6];
+  const int k = checkpoint_pieces(h, pc);
+  for (int j = 0; j < k; ++j) {
+    ALB_CUDA(cudaMemcpyAsync(p, pc[j].dev, pc[j].bytes, cudaMemcpyDeviceToHost, h->stream),
+             "alb_checkpoint_save: D2H");
+    p += pc[j].bytes;
+  }
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_checkpoint_save: synchronise");
+  return ALB_OK;
+}
+
+int alb_checkpoint_load(alb_handle* h, const void* buf) {
+  if (!h || !buf) return fail(ALB_EINVAL, "alb_checkpoint_load: null pointer");
+  CheckpointHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  if (memcmp(hd.magic, "ALBCKPT1", 8) != 0)
+    return fail(ALB_EINVAL, "alb_checkpoint_load: not a checkpoint of this library");
+  if (hd.nx != h->cfg.nx || hd.ny != h->cfg.ny || hd.precision != h->dev.precision ||
+      hd.warm != h->dev.prm.warm || hd.u_max != h->cfg.u_max || hd.bc_x != h->cfg.bc_x ||
+      hd.bc_y != h->cfg.bc_y || hd.ps != h->dev.ps)
+    return fail(ALB_EINVAL, "alb_checkpoint_load: checkpoint of another configuration");
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_checkpoint_load: synchronise");
+  const unsigned char* p = (const unsigned char*)buf + sizeof(hd);
+  Piece pc[6];
+  const int k = checkpoint_pieces(h, pc);
+  for (int j = 0; j < k; ++j) {
+    ALB_CUDA(cudaMemcpyAsync(pc[j].dev, p, pc[j].bytes, cudaMemcpyHostToDevice, h->stream),
+             "alb_checkpoint_load: H2D");
+    p += pc[j].bytes;
+  }
+  ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_checkpoint_load: synchronise");
+  h->steps = hd.steps;
+  h->initialised = true;
+  return ALB_OK;
+}
+
 int alb_totals(alb_handle* h, double* out) {
   if (!h || !out) return fail(ALB_EINVAL, "alb_totals: null pointer");
   if (!h->initialised) return fail(ALB_EINVAL, "alb_totals: call alb_init first");

@@ -85,6 +85,10 @@ cudaError_t launch_step(FlowDev& f, cudaStream_t s);
 cudaError_t launch_export_moments(const FlowDev& f, double* rho, double* rhoux, double* rhouy,
                                   double* rhoE, cudaStream_t s);
 cudaError_t launch_export_shifts(const FlowDev& f, signed char* ux, signed char* uy,
+                                 cudaStream_t s, bool next = false);
+// Planes [p0, p0 + np) of the current population (what = 0) or moment
+// (what = 1) buffer as FP64 planes of n values.
+cudaError_t launch_export_planes(const FlowDev& f, int what, int p0, int np, double* dst,
                                  cudaStream_t s);
 cudaError_t launch_equilibrium(const double* rho, const double* ubx, const double* uby,
                                const double* T, int n, double tol, int maxit, int precision,

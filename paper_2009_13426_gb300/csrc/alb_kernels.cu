@@ -150,6 +150,18 @@ __global__ void export_moments_kernel(const P* mom, size_t ps, size_t n, double 
   }
 }
 
+// Planes [p0, p0 + np) of a buffer (population or moment planes, stride ps)
+// as FP64 planes of n values each.
+template <typename P>
+__global__ void export_planes_kernel(const P* src, size_t ps, size_t n, int np, double* dst) {
+  const size_t total = (size_t)np * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = t / n, k = t - p * n;
+    dst[t] = (double)src[p * ps + k];
+  }
+}
+
 __global__ void export_shifts_kernel(const uint8_t* lat, size_t n, signed char* ux,
                                      signed char* uy) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
@@ -261,10 +273,26 @@ cudaError_t launch_export_moments(const FlowDev& f, double* rho, double* rhoux, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_export_shifts(const FlowDev& f, signed char* ux, signed char* uy,
+cudaError_t launch_export_planes(const FlowDev& f, int what, int p0, int np, double* dst,
                                  cudaStream_t s) {
+  const int buf = f.cur;
+  const void* base = what == 0 ? f.pop[buf] : f.mom[buf];
+  const size_t total = (size_t)np * f.n;
+  const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+  if (total == 0) return cudaSuccess;
+  if (f.precision == 0)
+    export_planes_kernel<double><<<blocks, 256, 0, s>>>((const double*)base + p0 * f.ps, f.ps,
+                                                        f.n, np, dst);
+  else
+    export_planes_kernel<float><<<blocks, 256, 0, s>>>((const float*)base + p0 * f.ps, f.ps,
+                                                       f.n, np, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_shifts(const FlowDev& f, signed char* ux, signed char* uy,
+                                 cudaStream_t s, bool next) {
   const int blocks = (int)((f.n + 255) / 256 < 4096 ? (f.n + 255) / 256 : 4096);
-  export_shifts_kernel<<<blocks, 256, 0, s>>>(f.lat[f.cur], f.n, ux, uy);
+  export_shifts_kernel<<<blocks, 256, 0, s>>>(next ? f.nxt[f.cur] : f.lat[f.cur], f.n, ux, uy);
   return cudaGetLastError();
 }
 

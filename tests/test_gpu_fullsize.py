@@ -1,0 +1,127 @@
+"""Full-size parity: the 4096^2 shear layer in the launch configuration the
+benchmark times (one flow, step_kernel, 128-node row blocks). The GPU state
+after a few steps is exported; for sampled nodes the oracle's own node
+functions redo one step from it - pull in the lattice the node selected, Grad
+rebuild of every pull whose sender lives in another lattice
+(ora_grad_populations with the sender's stored moments, central differences
+and relaxation time), collision (ora_collide_node) - and the result is
+compared with the GPU's next state, population by population. Sampled nodes
+include every kind of interface node (missing pulls) and random ones."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2009_13426_gb300 import flows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 4096
+NU = 1e-5
+
+
+@pytest.fixture(scope="module")
+def alb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_13426_gb300 import alb as A
+    A.lib()
+    return A
+
+
+@pytest.fixture(scope="module")
+def fields():
+    return flows.shear_layer(N)
+
+
+def oracle_node_step(cfg, xi, state, x, y):
+    """One step of node (x, y) from the exported state (post-collision
+    populations f, g in lattice `lat`, next lattice `nxt`, primitives)."""
+    f, g, lat_x, lat_y, nxt_x, nxt_y, rho, ux, uy, T = state
+    ny, nx = rho.shape
+    Ux, Uy = int(nxt_x[y, x]), int(nxt_y[y, x])
+    fp = np.empty(21)
+    gp = np.empty(21)
+    rebuilt = 0
+    for i in range(21):
+        sx = (x - xi[0][i] - Ux) % nx
+        sy = (y - xi[1][i] - Uy) % ny
+        if lat_x[sy, sx] == Ux and lat_y[sy, sx] == Uy:
+            fp[i] = f[i, sy, sx]
+            gp[i] = g[i, sy, sx]
+            continue
+        rebuilt += 1
+        xp, xm, yp, ym = (sx + 1) % nx, (sx - 1) % nx, (sy + 1) % ny, (sy - 1) % ny
+        du = np.array([[0.5 * (ux[sy, xp] - ux[sy, xm]), 0.5 * (uy[sy, xp] - uy[sy, xm])],
+                       [0.5 * (ux[yp, sx] - ux[ym, sx]), 0.5 * (uy[yp, sx] - uy[ym, sx])]])
+        dT = np.array([0.5 * (T[sy, xp] - T[sy, xm]), 0.5 * (T[yp, sx] - T[ym, sx])])
+        tau = 0.5 + NU / T[sy, sx]
+        st, fr, gr = O.grad_populations(cfg, Ux, Uy, rho[sy, sx], ux[sy, sx], uy[sy, sx],
+                                        T[sy, sx], du, dT, 1.0 - 1.0 / tau)
+        if st != O.OK:
+            return None
+        fp[i] = fr[i]
+        gp[i] = gr[i]
+    st, fs, gs = O.collide_node(cfg, fp, gp, Ux, Uy)
+    if st != O.OK:
+        return None
+    return fs, gs, rebuilt
+
+
+def export(fl):
+    f, g = fl.populations()
+    lx, ly = fl.shifts()
+    nx_, ny_ = fl.next_shifts()
+    return (f, g, lx, ly, nx_, ny_) + tuple(fl.primitives())
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (0, 1e-11)])
+def test_full_size_sampled_step(alb, fields, precision, tol):
+    fl = alb.Flow(N, N, u_max=2, nu=NU, precision=precision)
+    fl.init(*fields)
+    fl.step(3)
+    fl.sync()
+    before = export(fl)
+    fl.step(1)
+    fl.sync()
+    f1, g1 = fl.populations()
+    lat1 = fl.shifts()
+    fl.close()
+    # the lattice each node pulled into is the one it selected
+    assert np.array_equal(lat1[0], before[4]) and np.array_equal(lat1[1], before[5])
+    cfg = O.make_config(N, N, umax=2, nu=NU)
+    xi = O.velocities()
+    rng = np.random.default_rng(11)
+    # interface nodes: some pull comes from another lattice
+    lx, ly, nxx, nxy = before[2], before[3], before[4], before[5]
+    iface = np.zeros((N, N), bool)
+    for i in range(21):
+        for ux_ in range(-2, 3):
+            for uy_ in range(-2, 3):
+                sel = (nxx == ux_) & (nxy == uy_)
+                if not sel.any():
+                    continue
+                shx = np.roll(lx, (xi[1][i] + uy_, xi[0][i] + ux_), axis=(0, 1))
+                shy = np.roll(ly, (xi[1][i] + uy_, xi[0][i] + ux_), axis=(0, 1))
+                iface |= sel & ((shx != ux_) | (shy != uy_))
+    iy, ix = np.nonzero(iface)
+    assert iy.size > 0
+    pick = rng.choice(iy.size, size=min(150, iy.size), replace=False)
+    nodes = [(int(ix[k]), int(iy[k])) for k in pick]
+    nodes += [(int(rng.integers(N)), int(rng.integers(N))) for _ in range(150)]
+    worst = 0.0
+    checked = rebuilt = 0
+    for x, y in nodes:
+        r = oracle_node_step(cfg, xi, before, x, y)
+        if r is None:
+            continue
+        fs, gs, nreb = r
+        ref = np.concatenate([fs, gs])
+        got = np.concatenate([f1[:, y, x], g1[:, y, x]])
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        worst = max(worst, err)
+        checked += 1
+        rebuilt += nreb
+    assert checked >= 290
+    assert rebuilt > 0
+    assert worst <= tol, worst
