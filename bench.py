@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--side", "--n", dest="n", type=int, default=4096,
+                    help="grid side of the shear layer (--side under torchrun)")
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -174,6 +175,19 @@ def barrier(world):
         dist.barrier()
 
 
+def aggregate_mlups(world, nodes, steps, ms_max):
+    """Whole-job throughput: every rank advanced `nodes` nodes `steps` times;
+    the slowest rank's time bounds the job."""
+    return world * nodes * steps / (ms_max * 1e-3) / 1e6
+
+
+def workload_config(n, world):
+    return {"workload": "shear layer %dx%d periodic, Mach 2.5 cold stream, T ratio 3, "
+                        "nu 1e-5, FP32 populations, FP64 Newton" % (n, n),
+            "nodes": n * n, "u_max": 2, "l2_flush": "not needed: 5.7 GB state >> L2",
+            "parallelism": "replica per GPU" if world > 1 else "single GPU"}
+
+
 # ----------------------------------------------------------------- CPU oracle sample
 
 def oracle_sample(n, steps, warmup=1):
@@ -183,7 +197,7 @@ def oracle_sample(n, steps, warmup=1):
     the full flow's row mix (128 of n rows lie in the two layers)."""
     import oracle as O
     f = flows.shear_layer(n)
-    rows = 64
+    rows = min(64, max(8, n // 8))
     bands = {"uniform": 0, "layer": n // 4 - rows // 2}
     per_node = {}
     total_time = 0.0
@@ -219,7 +233,7 @@ def run_reference(args, world, rank):
         "ms_per_step": round(1e3 * args.n * args.n / (res["mlups"] * 1e6), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "shear layer %dx%d, FP64 CPU oracle" % (args.n, args.n)},
+        "config": workload_config(args.n, world),
         "cpu_baseline": {"value": round(res["mlups"], 4), "unit": UNIT, "cores": cores,
                          "kind": "oracle", "sample": res["sample"]},
         "e2e": {"value": round(res["mlups"], 4), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -440,7 +454,7 @@ def run_ours(args, world, rank, local):
     ms32, d32 = timed(fl32, args.steps, args.warmup)
     clk = clocks.stop()
     ms_max = dist_max(ms32, world)
-    mlups = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    mlups = aggregate_mlups(world, N, args.steps, ms_max)
     per_launch_ms = ms32 / args.steps
     slots = costmodel.fp64_slots(d32, "fp32")
     achieved_tflops = 2.0 * slots / args.steps / (per_launch_ms * 1e-3) / 1e12
@@ -530,10 +544,7 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "shear layer %dx%d periodic, Mach 2.5 cold stream, T ratio 3, "
-                               "nu 1e-5, FP32 populations, FP64 Newton" % (n, n),
-                   "nodes": N, "u_max": 2, "l2_flush": "not needed: 5.7 GB state >> L2",
-                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "config": workload_config(n, world),
         "roofline": {"bound": "alu", "achieved": round(achieved_tflops, 4),
                      "peak": round(costmodel.FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                      "frac": round(achieved_tflops / costmodel.FP64_PEAK_TFLOPS, 4),
