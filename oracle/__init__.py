@@ -29,6 +29,7 @@ class Config(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("sensor", ctypes.c_int),
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+        ("overlap", ctypes.c_double),
     ]
 
 
@@ -56,6 +57,9 @@ def lib():
         L.ora_targets.argtypes = [ctypes.c_double] * 4 + [_dp]
         L.ora_select_shift.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.ora_select_shift.restype = ctypes.c_int
+        L.ora_select_shift_kept.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double]
+        L.ora_select_shift_kept.restype = ctypes.c_int
         L.ora_node_moments.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
         L.ora_collide_node.argtypes = [ctypes.POINTER(Config), _dp, _dp, ctypes.c_int, ctypes.c_int,
                                        _dp, _dp]
@@ -84,7 +88,7 @@ def lib():
 
 def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=PERIODIC,
                 sensor=False, sensor_eps=(0.01, 0.1, 1.0), sensor_alpha=(1.05, 1.35, 1.6),
-                newton_tol=1e-12, newton_maxit=50):
+                newton_tol=1e-12, newton_maxit=50, overlap=0.0):
     c = Config()
     c.nx, c.ny, c.umax = nx, ny, umax
     c.nu, c.gamma, c.n0 = nu, gamma, n0
@@ -93,6 +97,7 @@ def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=
         c.sensor_eps[k] = sensor_eps[k]
         c.sensor_alpha[k] = sensor_alpha[k]
     c.newton_tol, c.newton_maxit = newton_tol, newton_maxit
+    c.overlap = overlap
     return c
 
 
@@ -120,6 +125,10 @@ def targets(rho, ubx, uby, T):
 
 def select_shift(u, n0=0.5, umax=2):
     return lib().ora_select_shift(float(u), float(n0), int(umax))
+
+
+def select_shift_kept(u, current, w, n0=0.5, umax=2):
+    return lib().ora_select_shift_kept(float(u), float(n0), int(umax), int(current), float(w))
 
 
 def node_moments(f, g, Ux, Uy, gamma=1.4):

@@ -220,6 +220,20 @@ int ora_select_shift(double u, double n0, int umax) {
   return u > 0.0 ? umax : -umax;
 }
 
+/* Overlapping ranges (Sec. III.A.2): the paper allows the range of a shift to
+ * be wider than 1, so that ranges of neighbouring shifts overlap; where they
+ * do, the shift a node already has is kept (its history). Here the range of
+ * the current shift is the criterion's interval widened by w on each side;
+ * outside it the node takes the criterion's shift. */
+int ora_select_shift_kept(double u, double n0, int umax, int current, double w) {
+  if (w > 0.0) {
+    const double lo = ((double)current - n0) - w;
+    const double hi = ((double)(current + 1) - n0) + w;
+    if (lo < u && u <= hi) return current;
+  }
+  return ora_select_shift(u, n0, umax);
+}
+
 /* Eq. polyTemp, evaluated with the populations' own velocities c_i = xi_i + U:
  * rho = sum f, rho u = sum f c, and T = [sum(|c|^2 f + g) - rho |u|^2] / (2 rho Cv).
  * Summing in the lattice frame (xi instead of c) gives the same T exactly in
@@ -366,6 +380,7 @@ static void central_diff(const ora_state* s, const double* F, int x, int y, doub
 
 ora_state* ora_create(const ora_config* cfg) {
   if (cfg->nx <= 0 || cfg->ny <= 0 || cfg->umax < 0 || cfg->umax > 3) return NULL;
+  if (!(cfg->overlap >= 0.0 && cfg->overlap <= 1.0)) return NULL;
   ora_state* s = (ora_state*)calloc(1, sizeof(ora_state));
   if (!s) return NULL;
   s->cfg = *cfg;
@@ -503,8 +518,10 @@ static int step_once(ora_state* s, const signed char* forced_x, const signed cha
         s->Unx[k] = forced_x[k];
         s->Uny[k] = forced_y[k];
       } else {
-        s->Unx[k] = (signed char)ora_select_shift(mom[1], c->n0, c->umax);
-        s->Uny[k] = (signed char)ora_select_shift(mom[2], c->n0, c->umax);
+        s->Unx[k] = (signed char)ora_select_shift_kept(mom[1], c->n0, c->umax, s->Ux[k],
+                                                       c->overlap);
+        s->Uny[k] = (signed char)ora_select_shift_kept(mom[2], c->n0, c->umax, s->Uy[k],
+                                                       c->overlap);
       }
     }
     s->stats.newton_calls += calls;

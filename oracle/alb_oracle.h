@@ -53,6 +53,9 @@ typedef struct {
   double sensor_alpha[3]; /* alpha at e1, e2 and 10 e2 (alpha = 1 up to e0) */
   double newton_tol;   /* max_k |G_k| / rho */
   int newton_maxit;
+  double overlap;      /* w >= 0: a node keeps the shift it has while u lies in that
+                          shift's range widened by w on both sides (overlapping
+                          ranges chosen by history, Sec. III.A.2); 0 = Eq. criterion */
 } ora_config;
 
 typedef struct {
@@ -80,6 +83,11 @@ void ora_targets(double rho, double ubx, double uby, double T, double m[ORA_M]);
 
 /* Shift criterion (Eq. criterion, with the n0 offset reading). */
 int ora_select_shift(double u, double n0, int umax);
+
+/* Shift selection with overlapping ranges (Sec. III.A.2, ranges wider than 1
+ * chosen by the node's history): keep `current` while
+ * current - n0 - w < u <= current + 1 - n0 + w, else Eq. criterion. */
+int ora_select_shift_kept(double u, double n0, int umax, int current, double w);
 
 /* Macroscopic moments of one node (Eq. polyTemp), populations in lattice U.
  * out = {rho, ux, uy, T} with u absolute (lattice-frame sums plus U). */

@@ -354,3 +354,54 @@ def test_replayed_lattice_decisions_reproduce_the_free_run():
     assert not np.array_equal(a.moments()[1], c.moments()[1])
     bad = np.full((n, n), 5, np.int8)
     assert b.step_forced(bad, bad) != O.OK
+
+
+# --------------------------------------------------------------- overlapping ranges
+
+@pytest.mark.parametrize("u,current,expect", [
+    # the paper's example: the range of U = 0 widened to [-1, 1] (w = 0.5)
+    (0.3, 0, 0), (0.99, 0, 0), (1.0, 0, 0), (-0.99, 0, 0),
+    (1.0 + 1e-12, 0, 1),        # leaves the widened range: the criterion's shift
+    (-1.0, 0, -1),              # lower end open: criterion gives -1 (-1.5 < u <= -0.5)
+    (0.01, 1, 1), (0.0, 1, 0),  # range of U = 1 is (0, 2]
+    (1.7, 0, 2),                # far outside: the criterion decides
+    (2.9, 2, 2), (-2.9, -2, -2),
+])
+def test_overlapping_ranges_keep_the_current_shift(u, current, expect):
+    assert O.select_shift_kept(u, current, 0.5) == expect
+
+
+def test_overlapping_ranges_with_zero_width_are_the_criterion():
+    rng = np.random.default_rng(5)
+    for u in rng.uniform(-3.2, 3.2, 2000):
+        for cur in (-2, -1, 0, 1, 2):
+            for n0 in (0.5, 0.51):
+                assert O.select_shift_kept(u, cur, 0.0, n0) == O.select_shift(u, n0)
+
+
+def test_overlapping_ranges_change_shift_only_outside_the_widened_range():
+    """Step by step on the Mach-1.2 vortex with w = 0.5: a node's next shift U'
+    always has u in (U' - 1, U' + 1]; it differs from its current shift U only
+    when u has left (U - 1, U + 1]. Fewer lattice changes and fewer rebuilt
+    pulls than with the plain criterion."""
+    n = 48
+    fields = flows.isentropic_vortex(n, n, radius=4.0, mach=1.2)
+    runs = {}
+    for w in (0.0, 0.5):
+        s = O.Simulation(O.make_config(n, n, overlap=w))
+        assert s.init(*fields) == O.OK
+        changes = 0
+        for _ in range(12):
+            r, ux, uy, T = s.primitives()
+            sx, sy = s.shifts()
+            assert s.step(1) == O.OK
+            nx_, ny_ = s.shifts()
+            for u, cur, new in ((ux, sx, nx_), (uy, sy, ny_)):
+                changes += int((new != cur).sum())
+                if w > 0:
+                    assert ((u > new - 1.0) & (u <= new + 1.0)).all()
+                    moved = new != cur
+                    assert not ((u[moved] > cur[moved] - 1.0) & (u[moved] <= cur[moved] + 1.0)).any()
+        runs[w] = (changes, s.stats()["reconstructions"])
+    assert runs[0.5][0] < runs[0.0][0]
+    assert runs[0.5][1] < runs[0.0][1]
