@@ -29,7 +29,7 @@ class Config(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("sensor", ctypes.c_int),
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
-        ("overlap", ctypes.c_double),
+        ("overlap", ctypes.c_double), ("overlap_rule", ctypes.c_int),
     ]
 
 
@@ -60,6 +60,9 @@ def lib():
         L.ora_select_shift_kept.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_double]
         L.ora_select_shift_kept.restype = ctypes.c_int
+        L.ora_select_shift_neighbours.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_double, ctypes.c_void_p, ctypes.c_int]
+        L.ora_select_shift_neighbours.restype = ctypes.c_int
         L.ora_node_moments.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
         L.ora_collide_node.argtypes = [ctypes.POINTER(Config), _dp, _dp, ctypes.c_int, ctypes.c_int,
                                        _dp, _dp]
@@ -88,7 +91,7 @@ def lib():
 
 def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=PERIODIC,
                 sensor=False, sensor_eps=(0.01, 0.1, 1.0), sensor_alpha=(1.05, 1.35, 1.6),
-                newton_tol=1e-12, newton_maxit=50, overlap=0.0):
+                newton_tol=1e-12, newton_maxit=50, overlap=0.0, overlap_rule=0):
     c = Config()
     c.nx, c.ny, c.umax = nx, ny, umax
     c.nu, c.gamma, c.n0 = nu, gamma, n0
@@ -98,6 +101,7 @@ def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=
         c.sensor_alpha[k] = sensor_alpha[k]
     c.newton_tol, c.newton_maxit = newton_tol, newton_maxit
     c.overlap = overlap
+    c.overlap_rule = overlap_rule
     return c
 
 
@@ -125,6 +129,15 @@ def targets(rho, ubx, uby, T):
 
 def select_shift(u, n0=0.5, umax=2):
     return lib().ora_select_shift(float(u), float(n0), int(umax))
+
+
+RULE_HISTORY, RULE_NEIGHBOURS = 0, 1
+
+
+def select_shift_neighbours(u, w, nb, n0=0.5, umax=2):
+    arr = (ctypes.c_int * len(nb))(*[int(v) for v in nb])
+    return lib().ora_select_shift_neighbours(float(u), float(n0), int(umax), float(w), arr,
+                                             len(nb))
 
 
 def select_shift_kept(u, current, w, n0=0.5, umax=2):

@@ -234,6 +234,32 @@ int ora_select_shift_kept(double u, double n0, int umax, int current, double w) 
   return ora_select_shift(u, n0, umax);
 }
 
+/* Overlapping ranges chosen by the neighbourhood (Sec. III.A.2): where the
+ * widened ranges of several shifts hold u, prefer the shift most of the eight
+ * surrounding nodes use, so that neighbours share a lattice and fewer nodes
+ * sit at an interface. The criterion's shift stays unless another candidate
+ * is used by strictly more neighbours. */
+int ora_select_shift_neighbours(double u, double n0, int umax, double w, const int* nb,
+                                int nnb) {
+  const int c = ora_select_shift(u, n0, umax);
+  if (!(w > 0.0)) return c;
+  int best = c, best_count = 0;
+  for (int j = 0; j < nnb; ++j) best_count += nb[j] == c;
+  for (int n = -umax; n <= umax; ++n) {
+    if (n == c) continue;
+    const double lo = ((double)n - n0) - w;
+    const double hi = ((double)(n + 1) - n0) + w;
+    if (!(lo < u && u <= hi)) continue;
+    int count = 0;
+    for (int j = 0; j < nnb; ++j) count += nb[j] == n;
+    if (count > best_count) {
+      best = n;
+      best_count = count;
+    }
+  }
+  return best;
+}
+
 /* Eq. polyTemp, evaluated with the populations' own velocities c_i = xi_i + U:
  * rho = sum f, rho u = sum f c, and T = [sum(|c|^2 f + g) - rho |u|^2] / (2 rho Cv).
  * Summing in the lattice frame (xi instead of c) gives the same T exactly in
@@ -381,6 +407,8 @@ static void central_diff(const ora_state* s, const double* F, int x, int y, doub
 ora_state* ora_create(const ora_config* cfg) {
   if (cfg->nx <= 0 || cfg->ny <= 0 || cfg->umax < 0 || cfg->umax > 3) return NULL;
   if (!(cfg->overlap >= 0.0 && cfg->overlap <= 1.0)) return NULL;
+  if (cfg->overlap_rule != ORA_RULE_HISTORY && cfg->overlap_rule != ORA_RULE_NEIGHBOURS)
+    return NULL;
   ora_state* s = (ora_state*)calloc(1, sizeof(ora_state));
   if (!s) return NULL;
   s->cfg = *cfg;
@@ -517,6 +545,23 @@ static int step_once(ora_state* s, const signed char* forced_x, const signed cha
       if (forced_x) {
         s->Unx[k] = forced_x[k];
         s->Uny[k] = forced_y[k];
+      } else if (c->overlap > 0.0 && c->overlap_rule == ORA_RULE_NEIGHBOURS) {
+        /* the current shifts of the eight surrounding nodes (boundary rule) */
+        const int x = k % nx, y = k / nx;
+        int nbx[8], nby[8], m = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            int gx, gy;
+            const int kk = resolve(y + dy, ny, c->bc_y, &gy) * nx + resolve(x + dx, nx, c->bc_x, &gx);
+            nbx[m] = s->Ux[kk];
+            nby[m] = s->Uy[kk];
+            ++m;
+          }
+        s->Unx[k] = (signed char)ora_select_shift_neighbours(mom[1], c->n0, c->umax, c->overlap,
+                                                             nbx, 8);
+        s->Uny[k] = (signed char)ora_select_shift_neighbours(mom[2], c->n0, c->umax, c->overlap,
+                                                             nby, 8);
       } else {
         s->Unx[k] = (signed char)ora_select_shift_kept(mom[1], c->n0, c->umax, s->Ux[k],
                                                        c->overlap);

@@ -53,10 +53,13 @@ typedef struct {
   double sensor_alpha[3]; /* alpha at e1, e2 and 10 e2 (alpha = 1 up to e0) */
   double newton_tol;   /* max_k |G_k| / rho */
   int newton_maxit;
-  double overlap;      /* w >= 0: a node keeps the shift it has while u lies in that
-                          shift's range widened by w on both sides (overlapping
-                          ranges chosen by history, Sec. III.A.2); 0 = Eq. criterion */
+  double overlap;      /* w in [0, 1]: each shift's range widened by w on both sides,
+                          so that ranges overlap (Sec. III.A.2); 0 = Eq. criterion */
+  int overlap_rule;    /* where ranges overlap: ORA_RULE_HISTORY keeps the node's shift,
+                          ORA_RULE_NEIGHBOURS takes the one most neighbours use */
 } ora_config;
+
+enum { ORA_RULE_HISTORY = 0, ORA_RULE_NEIGHBOURS = 1 };
 
 typedef struct {
   long long newton_calls;
@@ -88,6 +91,14 @@ int ora_select_shift(double u, double n0, int umax);
  * chosen by the node's history): keep `current` while
  * current - n0 - w < u <= current + 1 - n0 + w, else Eq. criterion. */
 int ora_select_shift_kept(double u, double n0, int umax, int current, double w);
+
+/* Shift selection with overlapping ranges chosen by the neighbourhood (Sec.
+ * III.A.2, to reduce interface cells): among the shifts n in [-umax, umax]
+ * whose widened range n - n0 - w < u <= n + 1 - n0 + w holds u, the one that
+ * most of the nb[0..nnb-1] neighbour shifts equal; Eq. criterion's shift
+ * unless another candidate is used by strictly more neighbours (candidates
+ * examined in increasing n). */
+int ora_select_shift_neighbours(double u, double n0, int umax, double w, const int* nb, int nnb);
 
 /* Macroscopic moments of one node (Eq. polyTemp), populations in lattice U.
  * out = {rho, ux, uy, T} with u absolute (lattice-frame sums plus U). */

@@ -77,6 +77,8 @@ def run_gpu(alb, nx, ny, fields, steps, precision, **kw):
         cfg["bc_y"] = bc[okw.pop("bc_y")]
     if "sensor" in okw:
         cfg["sensor"] = int(okw.pop("sensor"))
+    if "overlap" in okw:
+        cfg["shift_overlap"] = okw.pop("overlap")
     cfg.update(okw)
     fl = alb.Flow(nx, ny, **cfg)
     fl.init(*fields)
@@ -179,6 +181,29 @@ def test_vortex_fp32_maxwellian_start_matches_oracle(alb, vortex_oracle):
                           newton_start=alb.ALB_START_MAXWELLIAN)
     err = rel_errors(fl.moments(), s.moments())
     assert max(err.values()) <= FP32_TOL, err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vortex_overlapping_ranges_match_oracle(alb, precision):
+    """Shift ranges widened by 0.5 and chosen by history (Sec. III.A.2): FP64
+    plain against the free-running oracle (1e-11, shifts equal), FP32 form
+    with replayed decisions (1e-5)."""
+    fields = flows.isentropic_vortex()
+    kw = dict(umax=2, nu=1e-3, overlap=0.5)
+    if precision == 0:
+        s, st = run_oracle(64, 64, fields, 60, **kw)
+        assert st == O.OK
+        fl = run_gpu(alb, 64, 64, fields, 60, alb.ALB_FP64_PLAIN, **kw)
+        sx, sy = fl.shifts()
+        rx, ry = s.shifts()
+        assert (sx == rx).all() and (sy == ry).all()
+        tol = FP64_TOL
+        assert fl.stats()["reconstructions"] == s.stats()["reconstructions"]
+    else:
+        fl, s, _ = run_replay(alb, 64, 64, fields, 60, alb.ALB_FP32_FORM, **kw)
+        tol = FP32_TOL
+    err = rel_errors(fl.moments(), s.moments())
+    assert max(err.values()) <= tol, err
 
 
 def test_vortex_fp32_form_matches_oracle(alb, vortex_oracle):
