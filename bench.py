@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-overlap", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-flows", type=int, default=256,
@@ -505,6 +506,20 @@ def run_ours(args, world, rank, local):
     st = fl32.stats()
     fl32.close()
 
+    # the same flow with shift ranges widened by 0.5 and chosen by history
+    ovl = None
+    if not args.no_overlap:
+        flo = alb.Flow(n, n, u_max=2, nu=NU, precision=alb.ALB_FP32_FORM, stream=stream,
+                       shift_overlap=0.5)
+        flo.init(*fields)
+        mso, dso = timed(flo, args.steps, args.warmup)
+        ovl = {"shift_overlap": 0.5, "value": round(N * args.steps / (mso * 1e-3) / 1e6, 2),
+               "unit": UNIT, "ms_per_step": round(mso / args.steps, 3),
+               "rebuilt_pulls_per_node": round(dso["reconstructions"] / (N * args.steps), 4),
+               "rebuilt_pulls_per_node_criterion": round(d32["reconstructions"]
+                                                         / (N * args.steps), 4)}
+        flo.close()
+
     e2e = None
     if not args.no_e2e:
         pinned = [torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).pin_memory() for a in fields]
@@ -564,6 +579,8 @@ def run_ours(args, world, rank, local):
                                         "newton_failures", "reconstruction_failures")},
     }
     line.update(extra)
+    if ovl:
+        line["overlapping_ranges"] = ovl
     if batched:
         line["batched"] = batched
     if serve:

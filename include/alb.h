@@ -96,6 +96,10 @@ typedef struct alb_handle alb_handle; /* opaque */
  *                lattice of the solve; 8 more planes per buffer). The root is
  *                unique, so the start changes only the path and round-off;
  *                ALB_START_MAXWELLIAN follows the oracle's iteration.
+ *   shift_overlap w in [0, 1]: overlapping shift ranges chosen by history
+ *                (Sec. III.A.2): a node keeps its current shift U while
+ *                U - n0 - w < u <= U + 1 - n0 + w, and otherwise takes the
+ *                criterion's shift; 0 (the default) is Eq. criterion.
  *   stream       cudaStream_t to work on; NULL: the library creates one. */
 typedef struct {
   int nx, ny;
@@ -112,6 +116,7 @@ typedef struct {
   double newton_tol;
   int newton_maxit;
   int newton_start;
+  double shift_overlap;
   void* stream;
 } alb_config;
 
@@ -130,8 +135,8 @@ typedef struct {
 
 /* Fill *cfg with defaults: 64x64, D2Q21, u_max 2, nu 1e-3, gamma 1.4,
  * n0 0.5, FP64 plain, periodic, sensor off (eps 0.01/0.1/1, alpha
- * 1.05/1.35/1.6), tol 1e-12, 50 iterations, ALB_START_AUTO, library
- * stream. */
+ * 1.05/1.35/1.6), tol 1e-12, 50 iterations, ALB_START_AUTO, no range
+ * overlap, library stream. */
 int alb_config_default(alb_config* cfg);
 
 /* Create a flow: validates cfg and allocates two buffers of 42 population

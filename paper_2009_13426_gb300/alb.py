@@ -54,7 +54,8 @@ class alb_config(ctypes.Structure):
         ("bc_y", ctypes.c_int), ("sensor", ctypes.c_int),
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
-        ("newton_start", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("newton_start", ctypes.c_int), ("shift_overlap", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
     ]
 
 

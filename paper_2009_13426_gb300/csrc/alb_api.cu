@@ -107,6 +107,7 @@ int alb_config_default(alb_config* c) {
   c->newton_tol = 1e-12;
   c->newton_maxit = 50;
   c->newton_start = ALB_START_AUTO;
+  c->shift_overlap = 0.0;
   c->stream = nullptr;
   return ALB_OK;
 }
@@ -140,6 +141,8 @@ static int check_config(const alb_config* c) {
   if (c->newton_start != ALB_START_AUTO && c->newton_start != ALB_START_MAXWELLIAN &&
       c->newton_start != ALB_START_PREVIOUS)
     return fail(ALB_EINVAL, "unknown newton_start %d", c->newton_start);
+  if (!(c->shift_overlap >= 0.0 && c->shift_overlap <= 1.0))
+    return fail(ALB_EINVAL, "shift_overlap must be in [0, 1]");
   return ALB_OK;
 }
 
@@ -167,6 +170,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.sensor = cfg->sensor;
   p.maxit = cfg->newton_maxit;
   p.warm = uses_previous_start(cfg) ? 1 : 0;
+  p.overlap = cfg->shift_overlap;
   p.nu = cfg->nu;
   p.gamma = cfg->gamma;
   p.n0 = cfg->n0;

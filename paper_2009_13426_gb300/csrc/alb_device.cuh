@@ -51,6 +51,7 @@ struct Params {
   int maxit;
   int warm;          // 1: solves start from the previous step's multipliers
   double nu, gamma, n0, tol;
+  double overlap;    // widening of the current shift's range (0: Eq. criterion)
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
   double seps[3], salpha[3];
   double skx[4], sky[4];  // sensor knots: log10(eps) and alpha (host-computed)
@@ -65,6 +66,17 @@ __device__ __forceinline__ int select_shift_thr(double u, const Params& pr) {
   for (int t = 0; t < 6; ++t)
     if (t < 2 * pr.umax && u > pr.thr[t]) ++n;
   return n;
+}
+
+// Overlapping ranges chosen by history (Sec. III.A.2): keep the current shift
+// while current - n0 - w < u <= current + 1 - n0 + w, else Eq. criterion.
+__device__ __forceinline__ int select_shift_kept(double u, int current, const Params& pr) {
+  if (pr.overlap > 0.0) {
+    const double lo = ((double)current - pr.n0) - pr.overlap;
+    const double hi = ((double)(current + 1) - pr.n0) + pr.overlap;
+    if (lo < u && u <= hi) return current;
+  }
+  return select_shift_thr(u, pr);
 }
 
 // s + c * v with c a compile-time integer after unrolling: the zero and unit

@@ -197,7 +197,7 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   const double ubx = ajx.val() / rho, uby = ajy.val() / rho;
   const double T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
   const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
-  const int code2 = lat_code(select_shift_thr(ux, pr), select_shift_thr(uy, pr));
+  const int code2 = lat_code(select_shift_kept(ux, Ux, pr), select_shift_kept(uy, Uy, pr));
 
   double lam[NM];
   const int ns = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, cl.eq, lam, cnt)
