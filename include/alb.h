@@ -65,6 +65,7 @@ enum { ALB_FP64_PLAIN = 0, ALB_FP32_FORM = 1 };
 enum { ALB_PERIODIC = 0, ALB_ZERO_GRADIENT = 1 };
 enum { ALB_HOST = 0, ALB_DEVICE = 1 };
 enum { ALB_START_AUTO = 0, ALB_START_MAXWELLIAN = 1, ALB_START_PREVIOUS = 2 };
+enum { ALB_RULE_HISTORY = 0, ALB_RULE_NEIGHBOURS = 1 };
 
 typedef struct alb_handle alb_handle; /* opaque */
 
@@ -96,10 +97,16 @@ typedef struct alb_handle alb_handle; /* opaque */
  *                lattice of the solve; 8 more planes per buffer). The root is
  *                unique, so the start changes only the path and round-off;
  *                ALB_START_MAXWELLIAN follows the oracle's iteration.
- *   shift_overlap w in [0, 1]: overlapping shift ranges chosen by history
- *                (Sec. III.A.2): a node keeps its current shift U while
- *                U - n0 - w < u <= U + 1 - n0 + w, and otherwise takes the
- *                criterion's shift; 0 (the default) is Eq. criterion.
+ *   shift_overlap w in [0, 1]: each shift's range widened by w on both
+ *                sides, U - n0 - w < u <= U + 1 - n0 + w, so that the ranges
+ *                of neighbouring shifts overlap (Sec. III.A.2); 0 (the
+ *                default) is Eq. criterion.
+ *   shift_rule   where ranges overlap: ALB_RULE_HISTORY keeps the node's
+ *                current shift while its widened range holds u (else the
+ *                criterion's shift); ALB_RULE_NEIGHBOURS takes, among the
+ *                shifts whose widened range holds u, the one most of the
+ *                eight surrounding nodes currently use (the criterion's
+ *                shift unless another is used by strictly more).
  *   stream       cudaStream_t to work on; NULL: the library creates one. */
 typedef struct {
   int nx, ny;
@@ -117,6 +124,7 @@ typedef struct {
   int newton_maxit;
   int newton_start;
   double shift_overlap;
+  int shift_rule;
   void* stream;
 } alb_config;
 

@@ -108,6 +108,7 @@ int alb_config_default(alb_config* c) {
   c->newton_maxit = 50;
   c->newton_start = ALB_START_AUTO;
   c->shift_overlap = 0.0;
+  c->shift_rule = ALB_RULE_HISTORY;
   c->stream = nullptr;
   return ALB_OK;
 }
@@ -143,6 +144,8 @@ static int check_config(const alb_config* c) {
     return fail(ALB_EINVAL, "unknown newton_start %d", c->newton_start);
   if (!(c->shift_overlap >= 0.0 && c->shift_overlap <= 1.0))
     return fail(ALB_EINVAL, "shift_overlap must be in [0, 1]");
+  if (c->shift_rule != ALB_RULE_HISTORY && c->shift_rule != ALB_RULE_NEIGHBOURS)
+    return fail(ALB_EINVAL, "unknown shift_rule %d", c->shift_rule);
   return ALB_OK;
 }
 
@@ -171,6 +174,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.maxit = cfg->newton_maxit;
   p.warm = uses_previous_start(cfg) ? 1 : 0;
   p.overlap = cfg->shift_overlap;
+  p.rule = cfg->shift_rule;
   p.nu = cfg->nu;
   p.gamma = cfg->gamma;
   p.n0 = cfg->n0;

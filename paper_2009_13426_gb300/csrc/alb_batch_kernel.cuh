@@ -24,7 +24,9 @@ __global__ void __launch_bounds__(B, MINB)
   __shared__ double s_tab[EXPT_N];
   __shared__ __align__(16) unsigned long long s_args[sizeof(StepArgs<P>) / 8];
   __shared__ int s_item;
-  load_exptab(s_tab);
+  __shared__ RebuildQueue<B> s_rq;
+  if (threadIdx.x == 0) s_rq.count = 0;
+  load_exptab(s_tab);  // includes a barrier
   const StepArgs<P>& a = *reinterpret_cast<const StepArgs<P>*>(s_args);
   const Columns<P, B> cl(smem_raw);
   int it = blockIdx.x;
@@ -43,10 +45,8 @@ __global__ void __launch_bounds__(B, MINB)
       s_args[threadIdx.x] = src[threadIdx.x];
     }
     __syncthreads();
-    const int x = w.x0 + (int)(threadIdx.x & ((1u << w.tw_log2) - 1u));
-    const int y = w.y0 + (int)(threadIdx.x >> w.tw_log2);
     NodeCount nc;
-    if (x < a.prm.nx && y < a.prm.ny) node_step<P, B>(a, x, y, cl, s_tab, nc);
+    tile_step<P, B>(a, w.x0, w.y0, w.tw_log2, cl, s_tab, s_rq, nc);
     flush_counts(a.ctr, nc);
     if (!counter) it += gridDim.x;
   }
@@ -60,9 +60,9 @@ struct BatchKernel {
   static constexpr size_t smem() { return smem_bytes<P, B>(); }
   static int occupancy() {
     auto k = batch_step_kernel<P, B, MINB>;
-    if (smem() > 48 * 1024 &&
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()) !=
-            cudaSuccess)
+    // static shared memory counts against the default 48 KB too: always declare
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()) !=
+        cudaSuccess)
       return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, B, smem()) != cudaSuccess) return 0;

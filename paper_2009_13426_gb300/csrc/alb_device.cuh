@@ -50,6 +50,7 @@ struct Params {
   int sensor;
   int maxit;
   int warm;          // 1: solves start from the previous step's multipliers
+  int rule;          // where ranges overlap: 0 history, 1 neighbourhood
   double nu, gamma, n0, tol;
   double overlap;    // widening of the current shift's range (0: Eq. criterion)
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
@@ -77,6 +78,32 @@ __device__ __forceinline__ int select_shift_kept(double u, int current, const Pa
     if (lo < u && u <= hi) return current;
   }
   return select_shift_thr(u, pr);
+}
+
+// Overlapping ranges chosen by the neighbourhood (Sec. III.A.2): among the
+// shifts whose widened range holds u, the one most of the eight surrounding
+// nodes use (component `axis` of their lattice codes nb[0..7]); the
+// criterion's shift unless another candidate is used by strictly more.
+__device__ __forceinline__ int select_shift_neighbours(double u, int axis, const uint8_t nb[8],
+                                                       const Params& pr) {
+  const int c = select_shift_thr(u, pr);
+  int best = c, best_count = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) best_count += (axis ? lat_uy(nb[j]) : lat_ux(nb[j])) == c;
+  for (int n = -pr.umax; n <= pr.umax; ++n) {
+    if (n == c) continue;
+    const double lo = ((double)n - pr.n0) - pr.overlap;
+    const double hi = ((double)(n + 1) - pr.n0) + pr.overlap;
+    if (!(lo < u && u <= hi)) continue;
+    int count = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) count += (axis ? lat_uy(nb[j]) : lat_ux(nb[j])) == n;
+    if (count > best_count) {
+      best = n;
+      best_count = count;
+    }
+  }
+  return best;
 }
 
 // s + c * v with c a compile-time integer after unrolling: the zero and unit

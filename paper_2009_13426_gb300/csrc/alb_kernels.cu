@@ -24,12 +24,14 @@ __global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1)
     step_kernel(StepArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_tab[EXPT_N];
-  load_exptab(s_tab);
+  __shared__ RebuildQueue<BLOCK> s_rq;
+  if (threadIdx.x == 0) s_rq.count = 0;
+  load_exptab(s_tab);  // includes a barrier
   const Columns<P, BLOCK> cl(smem_raw);
-  const int x = blockIdx.x * BLOCK + threadIdx.x;
-  const int y = blockIdx.y;
+  constexpr int LG = BLOCK == 128 ? 7 : (BLOCK == 256 ? 8 : 6);
+  static_assert((1 << LG) == BLOCK, "row tiles of BLOCK nodes");
   NodeCount nc;
-  if (x < a.prm.nx) node_step<P, BLOCK>(a, x, y, cl, s_tab, nc);
+  tile_step<P, BLOCK>(a, blockIdx.x * BLOCK, blockIdx.y, LG, cl, s_tab, s_rq, nc);
   flush_counts(a.ctr, nc);
 }
 
@@ -117,8 +119,24 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
       P wbuf[NM];
 #pragma unroll
       for (int j = 0; j < NM; ++j) wbuf[j] = (P)lam[j];
+      // with the neighbourhood rule, the neighbours' initial lattices (Eq.
+      // criterion on their initial velocities, boundary rule outside the grid)
+      uint8_t nb[8];
+      if (pr.overlap > 0.0 && pr.rule == 1) {
+        int m = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            bool g2 = false;
+            const size_t kk = (size_t)resolve(y + dy, pr.ny, pr.bcy, &g2) * nx +
+                              resolve(x + dx, pr.nx, pr.bcx, &g2);
+            const double rr = a.rho[kk];
+            nb[m++] = (uint8_t)lat_code(select_shift(a.rhoux[kk] / rr, pr.n0, pr.umax),
+                                        select_shift(a.rhouy[kk] / rr, pr.n0, pr.umax));
+          }
+      }
       collide_store<P, BLOCK>(pr, cl, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out,
-                              s_tab, pr.warm ? wbuf : nullptr, a.lam_out, &cnt, &n_fail);
+                              s_tab, pr.warm ? wbuf : nullptr, a.lam_out, &cnt, &n_fail, nb);
     } else {
       for (int i = 0; i < NPLANES; ++i) a.pop_out[i * a.ps + k] = (P)0;
       a.mom_out[k] = (P)r;
@@ -219,10 +237,10 @@ __global__ void select_kernel(const double* rho, const double* rhou, int n, doub
 
 static dim3 grid_of(const Params& p) { return dim3((p.nx + BLOCK - 1) / BLOCK, p.ny); }
 
-// Dynamic shared memory above 48 KB needs an explicit opt-in per kernel.
+// Dynamic shared memory needs an explicit opt-in once static plus dynamic
+// shared memory exceed 48 KB; the dynamic size is always declared.
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

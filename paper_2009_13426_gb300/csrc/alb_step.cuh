@@ -174,7 +174,8 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
                                               P* __restrict__ mom_out, uint8_t* lat_out,
                                               uint8_t* nxt_out, const double* tab,
                                               const P* warm, P* lam_out,
-                                              SolveCount* cnt, unsigned* n_fail) {
+                                              SolveCount* cnt, unsigned* n_fail,
+                                              const uint8_t* nb = nullptr) {
   const P* st = cl.pop;
   const int Ux = lat_ux(code), Uy = lat_uy(code);
   Acc<P> ar, ajx, ajy, ae;
@@ -197,7 +198,12 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   const double ubx = ajx.val() / rho, uby = ajy.val() / rho;
   const double T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
   const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
-  const int code2 = lat_code(select_shift_kept(ux, Ux, pr), select_shift_kept(uy, Uy, pr));
+  // next lattice: Eq. criterion, or overlapping ranges chosen by history or
+  // by the neighbours' current lattices nb[0..7]
+  const bool by_nb = pr.overlap > 0.0 && pr.rule == 1 && nb;
+  const int code2 = by_nb ? lat_code(select_shift_neighbours(ux, 0, nb, pr),
+                                     select_shift_neighbours(uy, 1, nb, pr))
+                          : lat_code(select_shift_kept(ux, Ux, pr), select_shift_kept(uy, Uy, pr));
 
   double lam[NM];
   const int ns = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, cl.eq, lam, cnt)
@@ -255,6 +261,23 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   nxt_out[k] = (uint8_t)code2;
 }
 
+// Current lattices of the eight nodes around (x, y) (boundary rule for
+// positions outside the grid), in a fixed order.
+__device__ __forceinline__ void neighbour_codes(const Params& pr, const uint8_t* cur, int x, int y,
+                                                uint8_t nb[8]) {
+  int m = 0;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      bool gh = false;
+      const int rx = resolve(x + dx, pr.nx, pr.bcx, &gh);
+      const int ry = resolve(y + dy, pr.ny, pr.bcy, &gh);
+      nb[m++] = cur[(size_t)ry * pr.nx + rx];
+    }
+}
+
 // Counts of one node update, added to the flow's counters warp by warp.
 struct NodeCount {
   SolveCount solve;
@@ -271,56 +294,89 @@ __device__ __forceinline__ void flush_counts(unsigned long long* ctr, const Node
   warp_count(ctr + CTR_REC_FAIL, c.rec_fail);
 }
 
-// One time step of node (x, y) of a flow (Sec. IV.A.3): pull in the lattice
-// selected at the previous step, rebuild the missing pulls, collide, store.
+// Shared state of a block's rebuild queue: one entry (owner thread << 5 | i)
+// per missing pull of the block's nodes, at most Q per node.
+template <int B>
+struct RebuildQueue {
+  unsigned short entry[Q * B];
+  int count;
+};
+
+// One time step of the nodes of a tile (Sec. IV.A.3), one node per thread:
+// thread t updates node (x0 + (t & (2^lg - 1)), y0 + (t >> lg)) if it lies in
+// the grid. Phase 1 pulls every population whose sender lives in the node's
+// new lattice and queues the missing ones; phase 2 rebuilds the queued pulls
+// with all threads of the block (each Grad rebuild is a full equilibrium
+// solve, so spreading them keeps the warps of interface nodes from waiting on
+// a few lanes); phase 3 collides and stores. A rebuilt value depends only on
+// its inputs, not on the thread that computes it. All threads of the block
+// must call this (it holds two barriers).
 template <typename P, int B>
-__device__ __forceinline__ void node_step(const StepArgs<P>& a, int x, int y,
+__device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, int lg,
                                           const Columns<P, B>& cl, const double* s_tab,
-                                          NodeCount& nc) {
+                                          RebuildQueue<B>& rq, NodeCount& nc) {
   const Params& pr = a.prm;
-  const size_t k = (size_t)y * pr.nx + x;
   const size_t ps = a.ps;
-  const int code = a.nxt_in[k];
-  const int Upx = lat_ux(code), Upy = lat_uy(code);
-  // pull every population whose sender lives in the same lattice; record the
-  // missing ones (bit i) and rebuild them afterwards from a single call site
-  unsigned missing = 0;
+  const int t = threadIdx.x;
+  const int mask = (1 << lg) - 1;
+  const int x = x0 + (t & mask), y = y0 + (t >> lg);
+  const bool active = x < pr.nx && y < pr.ny;
+  size_t k = 0;
+  int code = 0;
+  if (active) {
+    k = (size_t)y * pr.nx + x;
+    code = a.nxt_in[k];
+    const int Upx = lat_ux(code), Upy = lat_uy(code);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int sx = x - XI_X(i) - Upx;
-    const int sy = y - XI_Y(i) - Upy;
-    bool gh = false;
-    const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
-    const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
-    const size_t ks = (size_t)ry * pr.nx + rx;
-    if (!gh && a.lat_in[ks] == code) {
-      cl.pop[i * B] = a.pop_in[i * ps + ks];
-      cl.pop[(Q + i) * B] = a.pop_in[(Q + i) * ps + ks];
-    } else {
-      missing |= 1u << i;
+    for (int i = 0; i < Q; ++i) {
+      const int sx = x - XI_X(i) - Upx;
+      const int sy = y - XI_Y(i) - Upy;
+      bool gh = false;
+      const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
+      const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
+      const size_t ks = (size_t)ry * pr.nx + rx;
+      if (!gh && a.lat_in[ks] == code) {
+        cl.pop[i * B] = a.pop_in[i * ps + ks];
+        cl.pop[(Q + i) * B] = a.pop_in[(Q + i) * ps + ks];
+      } else {
+        rq.entry[atomicAdd(&rq.count, 1)] = (unsigned short)((t << 5) | i);
+      }
     }
   }
-  while (missing) {
-    const int i = __ffs(missing) - 1;
-    missing &= missing - 1;
+  __syncthreads();
+  const int nq = rq.count;
+  P* pop0 = cl.pop - t;  // column 0 of the block
+  for (int e = t; e < nq; e += B) {
+    const int owner = rq.entry[e] >> 5, i = rq.entry[e] & 31;
+    const int ox = x0 + (owner & mask), oy = y0 + (owner >> lg);
+    const int ocode = a.nxt_in[(size_t)oy * pr.nx + ox];
+    const int Upx = lat_ux(ocode), Upy = lat_uy(ocode);
     const int cx = XI_X(i), cy = XI_Y(i);
     double fd, gd;
     nc.rec += 1;
-    nc.rec_fail += rebuild_pull<P, B>(pr, a.mom_in, ps, i, cx, cy, Upx, Upy, x - cx - Upx,
-                                      y - cy - Upy, &fd, &gd, s_tab, cl.eq, a.lam_in, a.lat_in,
+    nc.calls += 1;
+    nc.rec_fail += rebuild_pull<P, B>(pr, a.mom_in, ps, i, cx, cy, Upx, Upy, ox - cx - Upx,
+                                      oy - cy - Upy, &fd, &gd, s_tab, cl.eq, a.lam_in, a.lat_in,
                                       &nc.solve);
-    cl.pop[i * B] = (P)fd;
-    cl.pop[(Q + i) * B] = (P)gd;
+    pop0[i * B + owner] = (P)fd;
+    pop0[(Q + i) * B + owner] = (P)gd;
   }
-  P wbuf[NM];
-  const P* warm = nullptr;
-  if (pr.warm) {
-    load_warm<P>(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
-    warm = wbuf;
+  __syncthreads();
+  if (t == 0) rq.count = 0;  // ordered before the next use by the caller's barrier
+  if (active) {
+    const int Upx = lat_ux(code), Upy = lat_uy(code);
+    P wbuf[NM];
+    const P* warm = nullptr;
+    if (pr.warm) {
+      load_warm<P>(a.lam_in, ps, k, a.lat_in[k], Upx, Upy, wbuf);
+      warm = wbuf;
+    }
+    uint8_t nb[8];
+    if (pr.overlap > 0.0 && pr.rule == 1) neighbour_codes(pr, a.nxt_in, x, y, nb);
+    collide_store<P, B>(pr, cl, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,
+                        warm, a.lam_out, &nc.solve, &nc.fail, nb);
+    nc.calls += 1;
   }
-  collide_store<P, B>(pr, cl, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,
-                      warm, a.lam_out, &nc.solve, &nc.fail);
-  nc.calls += 1 + nc.rec;
 }
 
 }  // namespace alb

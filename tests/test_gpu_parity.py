@@ -79,6 +79,8 @@ def run_gpu(alb, nx, ny, fields, steps, precision, **kw):
         cfg["sensor"] = int(okw.pop("sensor"))
     if "overlap" in okw:
         cfg["shift_overlap"] = okw.pop("overlap")
+    if "overlap_rule" in okw:
+        cfg["shift_rule"] = okw.pop("overlap_rule")
     cfg.update(okw)
     fl = alb.Flow(nx, ny, **cfg)
     fl.init(*fields)
@@ -183,13 +185,14 @@ def test_vortex_fp32_maxwellian_start_matches_oracle(alb, vortex_oracle):
     assert max(err.values()) <= FP32_TOL, err
 
 
+@pytest.mark.parametrize("rule", [O.RULE_HISTORY, O.RULE_NEIGHBOURS])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_vortex_overlapping_ranges_match_oracle(alb, precision):
-    """Shift ranges widened by 0.5 and chosen by history (Sec. III.A.2): FP64
-    plain against the free-running oracle (1e-11, shifts equal), FP32 form
-    with replayed decisions (1e-5)."""
+def test_vortex_overlapping_ranges_match_oracle(alb, precision, rule):
+    """Shift ranges widened by 0.5 (Sec. III.A.2), chosen by history or by the
+    neighbourhood: FP64 plain against the free-running oracle (1e-11, shifts
+    and rebuild counts equal), FP32 form with replayed decisions (1e-5)."""
     fields = flows.isentropic_vortex()
-    kw = dict(umax=2, nu=1e-3, overlap=0.5)
+    kw = dict(umax=2, nu=1e-3, overlap=0.5, overlap_rule=rule)
     if precision == 0:
         s, st = run_oracle(64, 64, fields, 60, **kw)
         assert st == O.OK
@@ -204,6 +207,22 @@ def test_vortex_overlapping_ranges_match_oracle(alb, precision):
         tol = FP32_TOL
     err = rel_errors(fl.moments(), s.moments())
     assert max(err.values()) <= tol, err
+
+
+def test_neighbourhood_rule_at_zero_gradient_ends(alb):
+    """The neighbourhood rule reads ghost neighbours through the boundary
+    rule: a ragged grid with zero-gradient ends in x and y, FP64 plain."""
+    nx, ny = 45, 29
+    fields = flows.isentropic_vortex(nx, ny, strength=3.0, radius=5.0, mach=0.9, seed=7)
+    kw = dict(umax=2, nu=1e-3, overlap=0.4, overlap_rule=O.RULE_NEIGHBOURS,
+              bc_x=O.ZERO_GRADIENT, bc_y=O.ZERO_GRADIENT)
+    s, st = run_oracle(nx, ny, fields, 30, **kw)
+    fl = run_gpu(alb, nx, ny, fields, 30, alb.ALB_FP64_PLAIN, **kw)
+    sx, sy = fl.shifts()
+    rx, ry = s.shifts()
+    assert (sx == rx).all() and (sy == ry).all()
+    err = rel_errors(fl.moments(), s.moments())
+    assert max(err.values()) <= FP64_TOL, err
 
 
 def test_vortex_fp32_form_matches_oracle(alb, vortex_oracle):
