@@ -30,6 +30,7 @@ class Config(ctypes.Structure):
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("overlap", ctypes.c_double), ("overlap_rule", ctypes.c_int),
+        ("moments", ctypes.c_int),
     ]
 
 
@@ -54,6 +55,9 @@ def lib():
         L.ora_equilibrium.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp,
                                                               ctypes.POINTER(ctypes.c_int)]
         L.ora_equilibrium.restype = ctypes.c_int
+        L.ora_equilibrium4.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp,
+                                                               ctypes.POINTER(ctypes.c_int)]
+        L.ora_equilibrium4.restype = ctypes.c_int
         L.ora_targets.argtypes = [ctypes.c_double] * 4 + [_dp]
         L.ora_select_shift.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.ora_select_shift.restype = ctypes.c_int
@@ -91,7 +95,7 @@ def lib():
 
 def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=PERIODIC,
                 sensor=False, sensor_eps=(0.01, 0.1, 1.0), sensor_alpha=(1.05, 1.35, 1.6),
-                newton_tol=1e-12, newton_maxit=50, overlap=0.0, overlap_rule=0):
+                newton_tol=1e-12, newton_maxit=50, overlap=0.0, overlap_rule=0, moments=8):
     c = Config()
     c.nx, c.ny, c.umax = nx, ny, umax
     c.nu, c.gamma, c.n0 = nu, gamma, n0
@@ -102,6 +106,7 @@ def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=
     c.newton_tol, c.newton_maxit = newton_tol, newton_maxit
     c.overlap = overlap
     c.overlap_rule = overlap_rule
+    c.moments = moments
     return c
 
 
@@ -118,6 +123,15 @@ def equilibrium(rho, ubx, uby, T, tol=1e-12, maxit=50):
     feq = np.zeros(Q)
     it = ctypes.c_int(0)
     st = lib().ora_equilibrium(rho, ubx, uby, T, tol, maxit, lam, feq, ctypes.byref(it))
+    return st, lam, feq, it.value
+
+
+def equilibrium4(rho, ubx, uby, T, tol=1e-12, maxit=50):
+    """Reduced (4-moment) numerical equilibrium; returns (status, lambda, feq, iters)."""
+    lam = np.zeros(4)
+    feq = np.zeros(Q)
+    it = ctypes.c_int(0)
+    st = lib().ora_equilibrium4(rho, ubx, uby, T, tol, maxit, lam, feq, ctypes.byref(it))
     return st, lam, feq, it.value
 
 

@@ -209,6 +209,112 @@ int ora_equilibrium(double rho, double ubx, double uby, double T, double tol, in
   return status;
 }
 
+/* Reduced model (App. C.2): four constraints - mass, momentum and the
+ * trace of the energy, sum_i f xi_a xi_a = 2 rho E with the monatomic energy
+ * 2E = |ubar|^2 + D T - and the exponential family of Eq. feqNum_4Mom. The
+ * iteration is ora_equilibrium's (Maxwellian start with lambda_0 from the
+ * normalisation, Newton on the convex dual with Armijo backtracking, stop at
+ * max_k |G_k| / rho <= tol) on four multipliers. */
+static void exp_family4(const double l[4], double p[ORA_Q]) {
+  for (int i = 0; i < ORA_Q; ++i) {
+    const double x = XI[i][0], y = XI[i][1];
+    p[i] = exp(-(1.0 + l[0] + l[1] * x + l[2] * y + l[3] * (x * x + y * y)));
+  }
+}
+
+static double dual_value4(const double l[4], const double p[ORA_Q], const double m[4]) {
+  double F = 0.0;
+  for (int i = 0; i < ORA_Q; ++i) F += p[i];
+  for (int k = 0; k < 4; ++k) F += l[k] * m[k];
+  return F;
+}
+
+int ora_equilibrium4(double rho, double ubx, double uby, double T, double tol, int maxit,
+                     double lambda[4], double feq[ORA_Q], int* iters) {
+  *iters = 0;
+  if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ubx) ||
+      !isfinite(uby))
+    return ORA_EUNREALIZABLE;
+  const double m[4] = {1.0, ubx, uby, ubx * ubx + uby * uby + D_SPACE * T};
+  /* Maxwellian start: l1 = -ubar/T, l2 = 1/(2T), l0 from sum p = 1 */
+  lambda[0] = 0.0;
+  lambda[1] = -ubx / T;
+  lambda[2] = -uby / T;
+  lambda[3] = 0.5 / T;
+  double p[ORA_Q];
+  exp_family4(lambda, p);
+  double Z = 0.0;
+  for (int i = 0; i < ORA_Q; ++i) Z += p[i];
+  lambda[0] = log(Z);
+  exp_family4(lambda, p);
+  double F = dual_value4(lambda, p, m);
+  int status = ORA_ENEWTON;
+  int it = 0;
+  for (;;) {
+    double G[4] = {-m[0], -m[1], -m[2], -m[3]};
+    double H[4][4];
+    memset(H, 0, sizeof(H));
+    for (int i = 0; i < ORA_Q; ++i) {
+      const double x = XI[i][0], y = XI[i][1];
+      const double P[4] = {1.0, x, y, x * x + y * y};
+      for (int a = 0; a < 4; ++a) {
+        G[a] += p[i] * P[a];
+        for (int b = 0; b < 4; ++b) H[a][b] += p[i] * P[a] * P[b];
+      }
+    }
+    double gmax = 0.0;
+    for (int k = 0; k < 4; ++k) gmax = fmax(gmax, fabs(G[k]));
+    if (!isfinite(gmax)) { status = ORA_ESINGULAR; break; }
+    if (gmax <= tol) { status = ORA_OK; break; }
+    if (it >= maxit) { status = ORA_ENEWTON; break; }
+    /* Cholesky solve H d = G */
+    double L[4][4], y[4], d[4];
+    memset(L, 0, sizeof(L));
+    int ok = 1;
+    for (int j = 0; j < 4 && ok; ++j) {
+      double s = H[j][j];
+      for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+      if (!(s > 0.0) || !isfinite(s)) { ok = 0; break; }
+      L[j][j] = sqrt(s);
+      for (int i = j + 1; i < 4; ++i) {
+        double t = H[i][j];
+        for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+        L[i][j] = t / L[j][j];
+      }
+    }
+    if (!ok) { status = ORA_ESINGULAR; break; }
+    for (int i = 0; i < 4; ++i) {
+      double s = G[i];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+      y[i] = s / L[i][i];
+    }
+    for (int i = 3; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < 4; ++k) s -= L[k][i] * d[k];
+      d[i] = s / L[i][i];
+    }
+    double gd = 0.0;
+    for (int k = 0; k < 4; ++k) gd += G[k] * d[k];
+    double t = 1.0, lam_c[4], p_c[ORA_Q], F_c = 0.0;
+    int accepted = 0;
+    for (int ls = 0; ls < 40; ++ls) {
+      for (int k = 0; k < 4; ++k) lam_c[k] = lambda[k] + t * d[k];
+      exp_family4(lam_c, p_c);
+      F_c = dual_value4(lam_c, p_c, m);
+      if (isfinite(F_c) && F_c <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = 1; break; }
+      t *= 0.5;
+    }
+    ++it;
+    if (!accepted) { status = ORA_ENEWTON; break; }
+    for (int k = 0; k < 4; ++k) lambda[k] = lam_c[k];
+    for (int i = 0; i < ORA_Q; ++i) p[i] = p_c[i];
+    F = F_c;
+  }
+  *iters = it;
+  for (int i = 0; i < ORA_Q; ++i) feq[i] = rho * p[i];
+  return status;
+}
+
 /* Eq. criterion: U_a = n iff n - 0.5 < u_a <= n + 0.5. With an offset n0 the
  * interval is read as (n - n0, n + 1 - n0]; shifts are clamped to [-umax, umax]. */
 int ora_select_shift(double u, double n0, int umax) {
@@ -300,16 +406,26 @@ static double sensor_alpha(const ora_config* c, double eps) {
   return a[2];
 }
 
+/* Numerical equilibrium of the configured constraint set (8 or 4 moments). */
+static int equilibrium_cfg(const ora_config* c, double rho, double ubx, double uby, double T,
+                           double feq[ORA_Q]) {
+  int iters;
+  if (c->moments == 4) {
+    double l4[4];
+    return ora_equilibrium4(rho, ubx, uby, T, c->newton_tol, c->newton_maxit, l4, feq, &iters);
+  }
+  double lambda[ORA_M];
+  return ora_equilibrium(rho, ubx, uby, T, c->newton_tol, c->newton_maxit, lambda, feq, &iters);
+}
+
 /* Collision of one node (Eqs. coll, gEq, DeltaAvg) in its own lattice U. */
 int ora_collide_node(const ora_config* cfg, const double f[ORA_Q], const double g[ORA_Q],
                      int Ux, int Uy, double fs[ORA_Q], double gs[ORA_Q]) {
   double mom[4];
   ora_node_moments(f, g, Ux, Uy, cfg->gamma, mom);
   const double rho = mom[0], T = mom[3];
-  double lambda[ORA_M], feq[ORA_Q];
-  int iters;
-  int st = ora_equilibrium(rho, mom[1] - Ux, mom[2] - Uy, T, cfg->newton_tol, cfg->newton_maxit,
-                           lambda, feq, &iters);
+  double feq[ORA_Q];
+  int st = equilibrium_cfg(cfg, rho, mom[1] - Ux, mom[2] - Uy, T, feq);
   if (st != ORA_OK) {
     /* failure policy: the node is left uncollided */
     for (int i = 0; i < ORA_Q; ++i) { fs[i] = f[i]; gs[i] = g[i]; }
@@ -340,10 +456,8 @@ int ora_grad_populations(const ora_config* cfg, int Ux, int Uy, double rho, doub
                          double omega, double f[ORA_Q], double g[ORA_Q]) {
   const double Cv = 1.0 / (cfg->gamma - 1.0);
   const double Cp = cfg->gamma * Cv;
-  double lambda[ORA_M], feq[ORA_Q];
-  int iters;
-  int st = ora_equilibrium(rho, ux - Ux, uy - Uy, T, cfg->newton_tol, cfg->newton_maxit, lambda,
-                           feq, &iters);
+  double feq[ORA_Q];
+  int st = equilibrium_cfg(cfg, rho, ux - Ux, uy - Uy, T, feq);
   if (st != ORA_OK) return st;
   const double mu = rho * cfg->nu;
   const double kappa = rho * Cp * cfg->nu;
@@ -409,6 +523,7 @@ ora_state* ora_create(const ora_config* cfg) {
   if (!(cfg->overlap >= 0.0 && cfg->overlap <= 1.0)) return NULL;
   if (cfg->overlap_rule != ORA_RULE_HISTORY && cfg->overlap_rule != ORA_RULE_NEIGHBOURS)
     return NULL;
+  if (cfg->moments != 8 && cfg->moments != 4) return NULL;
   ora_state* s = (ora_state*)calloc(1, sizeof(ora_state));
   if (!s) return NULL;
   s->cfg = *cfg;

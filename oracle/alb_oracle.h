@@ -57,6 +57,8 @@ typedef struct {
                           so that ranges overlap (Sec. III.A.2); 0 = Eq. criterion */
   int overlap_rule;    /* where ranges overlap: ORA_RULE_HISTORY keeps the node's shift,
                           ORA_RULE_NEIGHBOURS takes the one most neighbours use */
+  int moments;         /* constraint set of the equilibrium: 8 (Eqs. G0_8mom..G3yaa_8mom,
+                          the default) or 4 (the reduced model, App. C.2) */
 } ora_config;
 
 enum { ORA_RULE_HISTORY = 0, ORA_RULE_NEIGHBOURS = 1 };
@@ -80,6 +82,14 @@ void ora_velocities(int xi_x[ORA_Q], int xi_y[ORA_Q]);
  * f^eq_i. Returns ORA_OK or an error code; *iters receives the Newton count. */
 int ora_equilibrium(double rho, double ubx, double uby, double T, double tol,
                     int maxit, double lambda[ORA_M], double feq[ORA_Q], int* iters);
+
+/* Reduced model (App. C.2, Eq. feqNum_4Mom): the numerical equilibrium
+ * f_i = rho exp[-(1 + l0 + l1x xi_x + l1y xi_y + l2 |xi|^2)] whose mass,
+ * momentum and energy trace sum_i f xi_a xi_a = 2 rho E = rho (|ubar|^2 + D T)
+ * (monatomic energy, D = 2) match the state; lambda order (0, x, y, |xi|^2).
+ * Same damped Newton and stopping rule as ora_equilibrium. */
+int ora_equilibrium4(double rho, double ubx, double uby, double T, double tol, int maxit,
+                     double lambda[4], double feq[ORA_Q], int* iters);
 
 /* Constraint targets M_k(rho, ubar, T) of Eqs. G0_8mom..G3yaa_8mom. */
 void ora_targets(double rho, double ubx, double uby, double T, double m[ORA_M]);

@@ -211,3 +211,64 @@ def test_lp_feasibility_agrees_with_convergence(u, T):
     feasible = lp.status == 0
     st, *_ = O.equilibrium(1.0, u, 0.0, T, maxit=200)
     assert feasible == (st == O.OK)
+
+
+# ---------------------------------------------------------------- reduced model (App. C.2)
+
+def _monomials4(x, y):
+    return np.array([np.ones_like(x), x, y, x * x + y * y])
+
+
+@pytest.mark.parametrize("T", [0.4, 0.7, 1.3])
+def test_reduced_model_at_rest_is_the_closed_form(T):
+    """At rest the four constraints and the eight coincide by symmetry; both
+    give rho e^{-a|xi|^2} / Z with the bisection parameter a."""
+    rho = 1.3
+    st, lam, feq, _ = O.equilibrium4(rho, 0.0, 0.0, T)
+    assert st == O.OK
+    a = _rest_parameter(T)
+    x, y = _xi()
+    w = np.exp(-a * (x * x + y * y))
+    np.testing.assert_allclose(feq, rho * w / w.sum(), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(lam[1:3], 0.0, atol=1e-11)
+    np.testing.assert_allclose(lam[3], a, rtol=1e-10)
+
+
+@pytest.mark.parametrize("state", _states(10, 13, umax=1.2))
+def test_reduced_model_is_the_constrained_exponential(state):
+    """Eq. feqNum_4Mom: mass, momentum and the energy trace
+    sum f xi_a xi_a = 2 rho E = rho (|u|^2 + D T) are met, and -1 - ln(f/rho)
+    is affine in (1, xi_x, xi_y, |xi|^2) with the returned multipliers; a
+    generic optimiser on the dual finds the same point."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    rho, ubx, uby, T = state
+    st, lam, feq, _ = O.equilibrium4(rho, ubx, uby, T)
+    assert st == O.OK
+    x, y = _xi()
+    P = _monomials4(x, y)
+    m = np.array([1.0, ubx, uby, ubx ** 2 + uby ** 2 + 2.0 * T])
+    np.testing.assert_allclose(P @ feq, rho * m, rtol=0, atol=1e-12 * rho * 10)
+    rhs = -1.0 - np.log(feq / rho)
+    coef, *_ = np.linalg.lstsq(P.T, rhs, rcond=None)
+    assert np.abs(P.T @ coef - rhs).max() < 1e-10
+    np.testing.assert_allclose(coef, lam, rtol=1e-8, atol=1e-8)
+
+    def F(l):
+        p = np.exp(-1.0 - l @ P)
+        return p.sum() + l @ m, m - P @ p
+
+    res = scipy_opt.minimize(F, np.array([0.0, 0.0, 0.0, 0.5 / T]), jac=True, method="BFGS",
+                             options={"gtol": 1e-13, "maxiter": 5000})
+    np.testing.assert_allclose(feq, rho * np.exp(-1.0 - res.x @ P), rtol=1e-7, atol=1e-12)
+
+
+def test_reduced_model_differs_from_eight_moments_away_from_rest():
+    """The reduced set leaves the pressure tensor and heat flux free: away from
+    rest its equilibrium is another point (Sec. C.2: convective terms are not
+    recovered), so the second-order moment xx differs from rho (u_x^2 + T)."""
+    rho, ubx, uby, T = 1.0, 0.6, 0.0, 0.7
+    _, _, f4, _ = O.equilibrium4(rho, ubx, uby, T)
+    _, _, f8, _ = O.equilibrium(rho, ubx, uby, T)
+    x, y = _xi()
+    assert abs((f8 * x * x).sum() - rho * (ubx ** 2 + T)) < 1e-11
+    assert abs((f4 * x * x).sum() - rho * (ubx ** 2 + T)) > 1e-4

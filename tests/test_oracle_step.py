@@ -73,10 +73,13 @@ def test_shift_criterion_paper_figure_examples():
 
 # ---------------------------------------------------------------- collision
 
+@pytest.mark.parametrize("moments", [8, 4])
 @pytest.mark.parametrize("sensor", [False, True])
-def test_collision_conserves_mass_momentum_energy(sensor):
+def test_collision_conserves_mass_momentum_energy(sensor, moments):
+    """Both constraint sets fix mass, momentum and the energy trace, so the
+    collision conserves mass, momentum and total energy with either."""
     rng = np.random.default_rng(9)
-    cfg = O.make_config(4, 4, nu=1e-3, sensor=sensor)
+    cfg = O.make_config(4, 4, nu=1e-3, sensor=sensor, moments=moments)
     x, y = _xi()
     for _ in range(25):
         Ux, Uy = (int(v) for v in rng.integers(-2, 3, 2))
