@@ -289,7 +289,8 @@ def run_batched(args):
         s1 = [fl.stats() for fl in b.flows]
         tot = {key: sum(x[key] - y[key] for x, y in zip(s1, s0))
                for key in ("fp64_evaluations", "fp32_iterations", "newton_calls",
-                           "reconstructions", "newton_failures", "reconstruction_failures")}
+                           "newton_iterations", "reconstructions", "newton_failures",
+                           "reconstruction_failures")}
         # the same flows one launch per flow and step (alb_step), same stream
         e0.record(stream)
         for fl in b.flows:
@@ -301,6 +302,9 @@ def run_batched(args):
         b.close()
     launches = k * (2 if tuning["dynamic"] else 1) + (k % 2)
     upd = nodes * k
+    tot["node_updates"] = upd
+    slots = costmodel.fp64_slots(tot, "fp32")
+    tflops = 2.0 * slots / (ms * 1e-3) / 1e12
     return {"workload": "256 periodic flows, side log-uniform 64-1024 (seed 4), vortex or "
                         "shear layer, Mach 0.5-3, T ratio 1-4, nu 1e-5..1e-3, FP32 form",
             "flows": len(specs), "nodes": nodes, "steps": k, "unit": UNIT,
@@ -310,7 +314,12 @@ def run_batched(args):
             "graph": "two steps per CUDA graph replay",
             "launches": launches, "tuning": tuning, "tune_seconds": round(tune_s, 1),
             "per_node": {key: round(v / upd, 4) for key, v in tot.items()
-                         if key not in ("newton_failures", "reconstruction_failures")},
+                         if key not in ("newton_failures", "reconstruction_failures",
+                                        "node_updates")},
+            "roofline": {"bound": "alu", "achieved": round(tflops, 4),
+                         "peak": round(costmodel.FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                         "frac": round(tflops / costmodel.FP64_PEAK_TFLOPS, 4),
+                         "kernel": "batch_step_kernel<float>"},
             "failures": {"node": tot["newton_failures"],
                          "rebuild": tot["reconstruction_failures"]}}
 

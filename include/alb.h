@@ -101,6 +101,10 @@ typedef struct alb_handle alb_handle; /* opaque */
  *                sides, U - n0 - w < u <= U + 1 - n0 + w, so that the ranges
  *                of neighbouring shifts overlap (Sec. III.A.2); 0 (the
  *                default) is Eq. criterion.
+ *   moments      constraint set of the numerical equilibrium: 8 (Eqs.
+ *                G0_8mom..G3yaa_8mom, the default) or 4 (the reduced model
+ *                of App. C.2, Eq. feqNum_4Mom: mass, momentum and the energy
+ *                trace; a 4x4 FP64 Newton in both precisions).
  *   shift_rule   where ranges overlap: ALB_RULE_HISTORY keeps the node's
  *                current shift while its widened range holds u (else the
  *                criterion's shift); ALB_RULE_NEIGHBOURS takes, among the
@@ -125,6 +129,7 @@ typedef struct {
   int newton_start;
   double shift_overlap;
   int shift_rule;
+  int moments;
   void* stream;
 } alb_config;
 
@@ -144,7 +149,7 @@ typedef struct {
 /* Fill *cfg with defaults: 64x64, D2Q21, u_max 2, nu 1e-3, gamma 1.4,
  * n0 0.5, FP64 plain, periodic, sensor off (eps 0.01/0.1/1, alpha
  * 1.05/1.35/1.6), tol 1e-12, 50 iterations, ALB_START_AUTO, no range
- * overlap, library stream. */
+ * overlap, 8 moments, library stream. */
 int alb_config_default(alb_config* cfg);
 
 /* Create a flow: validates cfg and allocates two buffers of 42 population

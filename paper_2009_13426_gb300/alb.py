@@ -57,7 +57,7 @@ class alb_config(ctypes.Structure):
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("newton_start", ctypes.c_int), ("shift_overlap", ctypes.c_double),
-        ("shift_rule", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("shift_rule", ctypes.c_int), ("moments", ctypes.c_int), ("stream", ctypes.c_void_p),
     ]
 
 

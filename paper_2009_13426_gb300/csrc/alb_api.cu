@@ -109,6 +109,7 @@ int alb_config_default(alb_config* c) {
   c->newton_start = ALB_START_AUTO;
   c->shift_overlap = 0.0;
   c->shift_rule = ALB_RULE_HISTORY;
+  c->moments = 8;
   c->stream = nullptr;
   return ALB_OK;
 }
@@ -146,6 +147,8 @@ static int check_config(const alb_config* c) {
     return fail(ALB_EINVAL, "shift_overlap must be in [0, 1]");
   if (c->shift_rule != ALB_RULE_HISTORY && c->shift_rule != ALB_RULE_NEIGHBOURS)
     return fail(ALB_EINVAL, "unknown shift_rule %d", c->shift_rule);
+  if (c->moments != 8 && c->moments != 4)
+    return fail(ALB_EINVAL, "moments must be 8 or 4");
   return ALB_OK;
 }
 
@@ -175,6 +178,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.warm = uses_previous_start(cfg) ? 1 : 0;
   p.overlap = cfg->shift_overlap;
   p.rule = cfg->shift_rule;
+  p.moments = cfg->moments;
   p.nu = cfg->nu;
   p.gamma = cfg->gamma;
   p.n0 = cfg->n0;
@@ -194,6 +198,10 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.sky[2] = cfg->sensor_alpha[1];
   p.sky[3] = cfg->sensor_alpha[2];
   for (int t = 0; t < 6; ++t) p.thr[t] = (double)(t - cfg->u_max + 1) - cfg->n0;
+  for (int j = 0; j < 7; ++j) {
+    p.wlo[j] = ((double)(j - 3) - cfg->n0) - cfg->shift_overlap;
+    p.whi[j] = ((double)(j - 2) - cfg->n0) + cfg->shift_overlap;
+  }
   d.precision = cfg->precision;
   d.n = (size_t)cfg->nx * cfg->ny;
   d.ps = (d.n + 63) / 64 * 64;

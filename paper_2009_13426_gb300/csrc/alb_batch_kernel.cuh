@@ -1,5 +1,5 @@
 // Batched step kernel: one launch advances every flow of a batch by one time
-// step. The per-node update is the single-flow kernel's (node_step), so the
+// step. The tile update is the single-flow kernel's (tile_step), so the
 // result of a node depends only on its flow's state, never on the batch, the
 // tile shape or the block size.
 //

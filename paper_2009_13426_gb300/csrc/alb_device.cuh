@@ -51,12 +51,14 @@ struct Params {
   int maxit;
   int warm;          // 1: solves start from the previous step's multipliers
   int rule;          // where ranges overlap: 0 history, 1 neighbourhood
+  int moments;       // constraint set: 8, or 4 (reduced model)
   double nu, gamma, n0, tol;
   double overlap;    // widening of the current shift's range (0: Eq. criterion)
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
   double seps[3], salpha[3];
   double skx[4], sky[4];  // sensor knots: log10(eps) and alpha (host-computed)
   double thr[6];          // criterion thresholds (t + 1) - n0, t = -umax .. umax - 1
+  double wlo[7], whi[7];  // widened range of shift n = j - 3: ((n - n0) - w, ((n + 1) - n0) + w]
 };
 
 // Eq. criterion with the host-computed thresholds of Params (the same IEEE
@@ -71,12 +73,9 @@ __device__ __forceinline__ int select_shift_thr(double u, const Params& pr) {
 
 // Overlapping ranges chosen by history (Sec. III.A.2): keep the current shift
 // while current - n0 - w < u <= current + 1 - n0 + w, else Eq. criterion.
+// The widened bounds come from the host (same IEEE operations as the oracle).
 __device__ __forceinline__ int select_shift_kept(double u, int current, const Params& pr) {
-  if (pr.overlap > 0.0) {
-    const double lo = ((double)current - pr.n0) - pr.overlap;
-    const double hi = ((double)(current + 1) - pr.n0) + pr.overlap;
-    if (lo < u && u <= hi) return current;
-  }
+  if (pr.overlap > 0.0 && pr.wlo[current + 3] < u && u <= pr.whi[current + 3]) return current;
   return select_shift_thr(u, pr);
 }
 
@@ -87,20 +86,19 @@ __device__ __forceinline__ int select_shift_kept(double u, int current, const Pa
 __device__ __forceinline__ int select_shift_neighbours(double u, int axis, const uint8_t nb[8],
                                                        const Params& pr) {
   const int c = select_shift_thr(u, pr);
-  int best = c, best_count = 0;
+  int cnt[7] = {0, 0, 0, 0, 0, 0, 0};  // neighbours per shift n = j - 3
 #pragma unroll
-  for (int j = 0; j < 8; ++j) best_count += (axis ? lat_uy(nb[j]) : lat_ux(nb[j])) == c;
-  for (int n = -pr.umax; n <= pr.umax; ++n) {
-    if (n == c) continue;
-    const double lo = ((double)n - pr.n0) - pr.overlap;
-    const double hi = ((double)(n + 1) - pr.n0) + pr.overlap;
-    if (!(lo < u && u <= hi)) continue;
-    int count = 0;
+  for (int j = 0; j < 8; ++j) cnt[(axis ? lat_uy(nb[j]) : lat_ux(nb[j])) + 3] += 1;
+  int best = c, best_count = cnt[c + 3];
+  // with w <= 1 only the criterion's neighbours c - 1 and c + 1 can also hold u
 #pragma unroll
-    for (int j = 0; j < 8; ++j) count += (axis ? lat_uy(nb[j]) : lat_ux(nb[j])) == n;
-    if (count > best_count) {
+  for (int d = -1; d <= 1; d += 2) {
+    const int n = c + d;
+    if (n < -pr.umax || n > pr.umax) continue;
+    if (!(pr.wlo[n + 3] < u && u <= pr.whi[n + 3])) continue;
+    if (cnt[n + 3] > best_count) {
       best = n;
-      best_count = count;
+      best_count = cnt[n + 3];
     }
   }
   return best;

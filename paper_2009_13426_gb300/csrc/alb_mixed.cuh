@@ -618,6 +618,146 @@ static __device__ __noinline__ int newton_fp64g(double ubx, double uby, double T
   }
 }
 
+// Reduced model (App. C.2, Eq. feqNum_4Mom): four constraints - mass,
+// momentum and the energy trace sum f xi_a xi_a = rho (|ubar|^2 + D T) - and
+// the exponential family in (1, xi_x, xi_y, |xi|^2). The multipliers are kept
+// in the 8-slot layout of the full set (lambda_xx = lambda_yy = l2, the rest
+// 0), so the grouped evaluation, the warm-start planes and the lattice shift
+// of the multipliers are shared. The iteration is the oracle's: Maxwellian
+// start with lambda_0 from the normalisation (or the warm multipliers),
+// Newton on the dual with Armijo backtracking, stop at max|G|/rho <= tol; the
+// 4x4 Jacobian is the 8x8 one of the groups projected on P3 + P5 = |xi|^2.
+__device__ __forceinline__ void expand4(const double l4[4], double l8[NM]) {
+  l8[0] = l4[0]; l8[1] = l4[1]; l8[2] = l4[2];
+  l8[3] = l4[3]; l8[4] = 0.0; l8[5] = l4[3]; l8[6] = 0.0; l8[7] = 0.0;
+}
+
+static __device__ __noinline__ int newton4_fp64g(double ubx, double uby, double T, double tol,
+                                                 int maxit, const double* tab, double* col,
+                                                 int stride, double lam[NM], int* iters,
+                                                 int* evals, const double* warm) {
+  *iters = 0;
+  *evals = 0;
+  if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
+  const double m[4] = {1.0, ubx, uby, ubx * ubx + uby * uby + 2.0 * T};
+  double l4[4], M[NM];
+  int ev = 0;
+  double F = 0.0;
+  if (warm) {
+    l4[0] = warm[0]; l4[1] = warm[1]; l4[2] = warm[2]; l4[3] = warm[3];
+    expand4(l4, lam);
+    eval_fp64(lam, tab, col, stride, M);
+    ev = 1;
+    F = M[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F = fma(l4[k], m[k], F);
+  }
+  if (!warm || !isfinite(F)) {
+    const double iT = 1.0 / T;
+    l4[0] = 0.0; l4[1] = -ubx * iT; l4[2] = -uby * iT; l4[3] = 0.5 * iT;
+    expand4(l4, lam);
+    eval_fp64(lam, tab, col, stride, M);
+    ev += 1;
+    const double Z = M[0];
+    l4[0] = log(Z);
+    const double iZ = 1.0 / Z;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) col[i * stride] *= iZ;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) M[k] *= iZ;
+    F = M[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F = fma(l4[k], m[k], F);
+  }
+  int it = 0;
+  for (;;) {
+    const double G[4] = {M[0] - m[0], M[1] - m[1], M[2] - m[2], (M[3] + M[5]) - m[3]};
+    double gmax = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gmax = fmax(gmax, fabs(G[k]));
+    if (!isfinite(gmax)) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_SINGULAR; }
+    if (gmax <= tol) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_OK; }
+    if (it >= maxit) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_MAXIT; }
+    double H8[36];
+    jacobian_grouped(col, stride, H8);
+    // projection on P4 = (P0, P1, P2, P3 + P5) (packed lower triangles)
+    double H[10];
+    H[tri(0, 0)] = H8[tri(0, 0)];
+    H[tri(1, 0)] = H8[tri(1, 0)];
+    H[tri(1, 1)] = H8[tri(1, 1)];
+    H[tri(2, 0)] = H8[tri(2, 0)];
+    H[tri(2, 1)] = H8[tri(2, 1)];
+    H[tri(2, 2)] = H8[tri(2, 2)];
+    H[tri(3, 0)] = H8[tri(3, 0)] + H8[tri(5, 0)];
+    H[tri(3, 1)] = H8[tri(3, 1)] + H8[tri(5, 1)];
+    H[tri(3, 2)] = H8[tri(3, 2)] + H8[tri(5, 2)];
+    H[tri(3, 3)] = H8[tri(3, 3)] + 2.0 * H8[tri(5, 3)] + H8[tri(5, 5)];
+    bool ok = true;
+    double il[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double d = H[tri(j, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d = fma(-H[tri(j, k)], H[tri(j, k)], d);
+      ok = ok && (d > 0.0);
+      const double l = sqrt(fmax(d, 1e-300));
+      il[j] = 1.0 / l;
+      H[tri(j, j)] = l;
+#pragma unroll
+      for (int i = j + 1; i < 4; ++i) {
+        double s = H[tri(i, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = fma(-H[tri(i, k)], H[tri(j, k)], s);
+        H[tri(i, j)] = s * il[j];
+      }
+    }
+    if (!ok) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_SINGULAR; }
+    double d[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double s = G[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fma(-H[tri(i, k)], d[k], s);
+      d[i] = s * il[i];
+    }
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      double s = d[i];
+#pragma unroll
+      for (int k = i + 1; k < 4; ++k) s = fma(-H[tri(k, i)], d[k], s);
+      d[i] = s * il[i];
+    }
+    double gd = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gd = fma(G[k], d[k], gd);
+    double t = 1.0, Fc = 0.0, lc[4];
+    bool accepted = false;
+    for (int ls = 0; ls < 40; ++ls) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lc[k] = fma(t, d[k], l4[k]);
+      expand4(lc, lam);
+      eval_fp64(lam, tab, col, stride, M);
+      ++ev;
+      Fc = M[0];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Fc = fma(lc[k], m[k], Fc);
+      if (isfinite(Fc) && Fc <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = true; break; }
+      t *= 0.5;
+    }
+    ++it;
+    if (!accepted) {
+      expand4(l4, lam);
+      eval_fp64(lam, tab, col, stride, M);
+      *iters = it;
+      *evals = ev + 1;
+      return NEWTON_MAXIT;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) l4[k] = lc[k];
+    F = Fc;
+  }
+}
+
 // Equilibrium of the FP32 form: FP32 Newton (from the warm start if given,
 // else from the Maxwellian; again from the Maxwellian if the warm start
 // fails), FP64 refinement, full FP64 Newton as the last fallback. The FP64

@@ -41,6 +41,24 @@ template <typename P, int B = BLOCK>
 __device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, double uby,
                                                 double T, const double* tab, const P* warm,
                                                 double* eq, double lam[NM], SolveCount* cnt) {
+  if (pr.moments == 4) {
+    // reduced model: FP64 4x4 Newton in both precisions
+    double w8[NM];
+    if (warm)
+#pragma unroll
+      for (int k = 0; k < NM; ++k) w8[k] = (double)warm[k];
+    int it = 0, ev = 0;
+    int st = newton4_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev,
+                           warm ? w8 : nullptr);
+    cnt->fp64_iters += it;
+    cnt->fp64_evals += ev;
+    if (warm && st != NEWTON_OK && st != NEWTON_UNREALIZABLE) {
+      st = newton4_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev, nullptr);
+      cnt->fp64_iters += it;
+      cnt->fp64_evals += ev;
+    }
+    return st;
+  }
   if constexpr (std::is_same<P, float>::value) {
     return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, eq, B, lam, cnt);
   } else {

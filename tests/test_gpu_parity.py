@@ -209,6 +209,29 @@ def test_vortex_overlapping_ranges_match_oracle(alb, precision, rule):
     assert max(err.values()) <= tol, err
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vortex_reduced_model_matches_oracle(alb, precision):
+    """The reduced 4-moment equilibrium (App. C.2): FP64 plain against the
+    free-running oracle (1e-11, shifts equal), FP32 form with replayed
+    decisions (1e-5); 64^2 vortex, 60 steps."""
+    fields = flows.isentropic_vortex()
+    kw = dict(umax=2, nu=1e-3, moments=4)
+    if precision == 0:
+        s, st = run_oracle(64, 64, fields, 60, **kw)
+        assert st == O.OK
+        fl = run_gpu(alb, 64, 64, fields, 60, alb.ALB_FP64_PLAIN, **kw)
+        sx, sy = fl.shifts()
+        rx, ry = s.shifts()
+        assert (sx == rx).all() and (sy == ry).all()
+        assert fl.stats()["reconstructions"] == s.stats()["reconstructions"]
+        tol = FP64_TOL
+    else:
+        fl, s, _ = run_replay(alb, 64, 64, fields, 60, alb.ALB_FP32_FORM, **kw)
+        tol = FP32_TOL
+    err = rel_errors(fl.moments(), s.moments())
+    assert max(err.values()) <= tol, err
+
+
 def test_neighbourhood_rule_at_zero_gradient_ends(alb):
     """The neighbourhood rule reads ghost neighbours through the boundary
     rule: a ragged grid with zero-gradient ends in x and y, FP64 plain."""
