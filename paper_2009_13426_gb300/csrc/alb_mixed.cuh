@@ -626,7 +626,8 @@ static __device__ __noinline__ int newton_fp64g(double ubx, double uby, double T
 // of the multipliers are shared. The iteration is the oracle's: Maxwellian
 // start with lambda_0 from the normalisation (or the warm multipliers),
 // Newton on the dual with Armijo backtracking, stop at max|G|/rho <= tol; the
-// 4x4 Jacobian is the 8x8 one of the groups projected on P3 + P5 = |xi|^2.
+// 4x4 Jacobian takes its entries from the constraint sums of the evaluation
+// plus sum p |xi|^4.
 __device__ __forceinline__ void expand4(const double l4[4], double l8[NM]) {
   l8[0] = l4[0]; l8[1] = l4[1]; l8[2] = l4[2];
   l8[3] = l4[3]; l8[4] = 0.0; l8[5] = l4[3]; l8[6] = 0.0; l8[7] = 0.0;
@@ -678,20 +679,26 @@ static __device__ __noinline__ int newton4_fp64g(double ubx, double uby, double 
     if (!isfinite(gmax)) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_SINGULAR; }
     if (gmax <= tol) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_OK; }
     if (it >= maxit) { expand4(l4, lam); *iters = it; *evals = ev; return NEWTON_MAXIT; }
-    double H8[36];
-    jacobian_grouped(col, stride, H8);
-    // projection on P4 = (P0, P1, P2, P3 + P5) (packed lower triangles)
+    // Jacobian sum p P4 P4^T: all but sum p |xi|^4 are the sums of the last
+    // evaluation (P4 = (1, x, y, x^2 + y^2)); |xi|^4 is a^4 on an axis pair and
+    // 4 a^4 on a diagonal quadruple of the velocity set
+    const double sr4 =
+        (col[1 * stride] + col[3 * stride]) + (col[2 * stride] + col[4 * stride]) +
+        16.0 * ((col[9 * stride] + col[11 * stride]) + (col[10 * stride] + col[12 * stride])) +
+        81.0 * ((col[17 * stride] + col[19 * stride]) + (col[18 * stride] + col[20 * stride])) +
+        4.0 * ((col[5 * stride] + col[6 * stride]) + (col[7 * stride] + col[8 * stride])) +
+        64.0 * ((col[13 * stride] + col[14 * stride]) + (col[15 * stride] + col[16 * stride]));
     double H[10];
-    H[tri(0, 0)] = H8[tri(0, 0)];
-    H[tri(1, 0)] = H8[tri(1, 0)];
-    H[tri(1, 1)] = H8[tri(1, 1)];
-    H[tri(2, 0)] = H8[tri(2, 0)];
-    H[tri(2, 1)] = H8[tri(2, 1)];
-    H[tri(2, 2)] = H8[tri(2, 2)];
-    H[tri(3, 0)] = H8[tri(3, 0)] + H8[tri(5, 0)];
-    H[tri(3, 1)] = H8[tri(3, 1)] + H8[tri(5, 1)];
-    H[tri(3, 2)] = H8[tri(3, 2)] + H8[tri(5, 2)];
-    H[tri(3, 3)] = H8[tri(3, 3)] + 2.0 * H8[tri(5, 3)] + H8[tri(5, 5)];
+    H[tri(0, 0)] = M[0];
+    H[tri(1, 0)] = M[1];
+    H[tri(1, 1)] = M[3];
+    H[tri(2, 0)] = M[2];
+    H[tri(2, 1)] = M[4];
+    H[tri(2, 2)] = M[5];
+    H[tri(3, 0)] = M[3] + M[5];
+    H[tri(3, 1)] = M[6];
+    H[tri(3, 2)] = M[7];
+    H[tri(3, 3)] = sr4;
     bool ok = true;
     double il[4];
 #pragma unroll
