@@ -124,6 +124,21 @@ def entropy_spot(n=100, u0=2.0, amp=1e-3, rho0=1.0, T0=0.7, gamma=GAMMA):
                      T0 * (1.0 + amp * g), gamma)
 
 
+def acoustic_pulse(n=100, u0=0.3, amp=1e-3, rho0=1.0, T0=0.7, gamma=GAMMA):
+    """Sec. IV.B.3: Gaussian pressure pulse P = P0 (1 + A e^{-r^2}),
+    r^2 = |x - x_c|^2 / R^2 with R = n / 10, in a uniform x-flow; density and
+    temperature from the isentropic relations rho = rho0 (P/P0)^(1/gamma),
+    T = T0 (rho/rho0)^(gamma - 1), P0 = rho0 T0."""
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    R = n / 10.0
+    r2 = ((x - n / 2.0) ** 2 + (y - n / 2.0) ** 2) / R ** 2
+    P0 = rho0 * T0
+    P = P0 * (1.0 + amp * np.exp(-r2))
+    rho = rho0 * (P / P0) ** (1.0 / gamma)
+    T = T0 * (rho / rho0) ** (gamma - 1.0)
+    return conserved(rho, np.full_like(x, u0), np.zeros_like(x), T, gamma)
+
+
 # --------------------------------------------------------------------------
 # Batched and serving workloads
 
