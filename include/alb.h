@@ -60,7 +60,7 @@ extern "C" {
 #define ALB_ECUDA (-8)          /* CUDA runtime error (message in alb_last_error) */
 #define ALB_ENOTFOUND (-9)      /* unknown request id */
 
-enum { ALB_D2Q21 = 21 };
+enum { ALB_D2Q21 = 21, ALB_D2Q49 = 49 };
 enum { ALB_FP64_PLAIN = 0, ALB_FP32_FORM = 1 };
 enum { ALB_PERIODIC = 0, ALB_ZERO_GRADIENT = 1 };
 enum { ALB_HOST = 0, ALB_DEVICE = 1 };
@@ -71,7 +71,12 @@ typedef struct alb_handle alb_handle; /* opaque */
 
 /* Configuration of one flow.
  *   nx, ny       grid size (>= 1 each).
- *   stencil      ALB_D2Q21 (only one supported).
+ *   stencil      ALB_D2Q21, the adaptive lattice of the paper; or ALB_D2Q49,
+ *                the lattice {-3..3}^2 of its reference solver (App. C.1,
+ *                Sec. IV.B) with moments = 13, ALB_FP64_PLAIN, Maxwellian
+ *                starts, one flow per handle (no batches, no server); the
+ *                step is the same adaptive algorithm. D2Q49 velocity
+ *                (x, y) has index (x + 3) + 7 (y + 3).
  *   u_max        shift set {-u_max..u_max}^2, 0 <= u_max <= 3.
  *   nu           kinematic viscosity (>= 0); tau = 1/2 + nu/T.
  *   gamma        specific heat ratio gamma_r (> 1).
@@ -104,13 +109,24 @@ typedef struct alb_handle alb_handle; /* opaque */
  *   moments      constraint set of the numerical equilibrium: 8 (Eqs.
  *                G0_8mom..G3yaa_8mom, the default) or 4 (the reduced model
  *                of App. C.2, Eq. feqNum_4Mom: mass, momentum and the energy
- *                trace; a 4x4 FP64 Newton in both precisions).
+ *                trace; a 4x4 FP64 Newton in both precisions) on D2Q21; 13
+ *                (Eqs. G0..G4yyaa: moments up to third order and the trace
+ *                of the fourth, Eq. feqNum_13Mom with the x^3 monomial the
+ *                printed exponent omits) on D2Q49.
  *   shift_rule   where ranges overlap: ALB_RULE_HISTORY keeps the node's
  *                current shift while its widened range holds u (else the
  *                criterion's shift); ALB_RULE_NEIGHBOURS takes, among the
  *                shifts whose widened range holds u, the one most of the
  *                eight surrounding nodes currently use (the criterion's
  *                shift unless another is used by strictly more).
+ *   prandtl      Prandtl number Pr > 0. 1 (the default) is the BGK collision
+ *                of Eq. coll. Otherwise the collision of App. E (Eqs. Shakhov,
+ *                prandtlPoly) adds (1/tau - 1/tau_Pr) times a heat-flux term,
+ *                tau_Pr = 1/2 + (nu/Pr)/T, q = 1/2 sum cbar (|cbar|^2 f + g)
+ *                of the pre-collision populations; Grad's heat flux (Eq.
+ *                GradGeneral_f) takes kappa = rho Cp nu / Pr, and a rebuilt
+ *                pull is that collision applied to the Grad population. The
+ *                sensor factor scales tau and tau_Pr alike.
  *   stream       cudaStream_t to work on; NULL: the library creates one. */
 typedef struct {
   int nx, ny;
@@ -130,6 +146,7 @@ typedef struct {
   double shift_overlap;
   int shift_rule;
   int moments;
+  double prandtl;
   void* stream;
 } alb_config;
 
@@ -149,7 +166,7 @@ typedef struct {
 /* Fill *cfg with defaults: 64x64, D2Q21, u_max 2, nu 1e-3, gamma 1.4,
  * n0 0.5, FP64 plain, periodic, sensor off (eps 0.01/0.1/1, alpha
  * 1.05/1.35/1.6), tol 1e-12, 50 iterations, ALB_START_AUTO, no range
- * overlap, 8 moments, library stream. */
+ * overlap, 8 moments, Pr 1, library stream. */
 int alb_config_default(alb_config* cfg);
 
 /* Create a flow: validates cfg and allocates two buffers of 42 population
@@ -185,9 +202,9 @@ int alb_shifts(alb_handle* h, signed char* ux, signed char* uy, int where);
 int alb_next_shifts(alb_handle* h, signed char* ux, signed char* uy, int where);
 
 /* Post-collision populations of the current state as FP64 planes:
- * f[i * n + k], g[i * n + k] for velocity i (order of alb_velocities) and
- * node k = y * nx + x, n = nx * ny; 21 planes each. They live in the lattice
- * of alb_shifts. */
+ * f[i * n + k], g[i * n + k] for velocity i (order of
+ * alb_stencil_velocities) and node k = y * nx + x, n = nx * ny; 21 planes
+ * each (49 on D2Q49). They live in the lattice of alb_shifts. */
 int alb_populations(alb_handle* h, double* f, double* g, int where);
 
 /* Primitive moments stored with the current state (rho, u_x, u_y, T; the
@@ -277,6 +294,19 @@ int alb_select_shift(const double* rho, const double* rhou, int n, double n0, in
 
 /* D2Q21 velocity table used by every entry point (host memory, 21 each). */
 int alb_velocities(int* xi_x, int* xi_y);
+
+/* Velocity table of a stencil (ALB_D2Q21: 21 entries, ALB_D2Q49: 49) into
+ * host arrays; ALB_EUNSUPPORTED for another stencil. */
+int alb_stencil_velocities(int stencil, int* xi_x, int* xi_y);
+
+/* The reference solver's equilibrium (App. C.1) on D2Q49 for n states in the
+ * lattice frame, FP64 damped Newton on the 13 multipliers (order 1, x, y,
+ * xx, xy, yy, xxx, xxy, xyy, yyy, xx|xi|^2, xy|xi|^2, yy|xi|^2), stop at
+ * max|G|/rho <= tol. Device arrays: feq[k*49 + i], lambda[k*13 + j],
+ * iters[k], status[k] (codes of alb_equilibrium); all required. */
+int alb_equilibrium13(const double* rho, const double* ubx, const double* uby, const double* T,
+                      int n, double tol, int maxit, double* feq, double* lambda, int* iters,
+                      int* status, void* stream);
 
 /* ------------------------------------------------------------------------
  * Batched flows. Many independent flows, each with its own grid size and

@@ -13,6 +13,9 @@ from . import build as _build
 
 Q = 21
 M = 8
+Q49 = 49
+M13 = 13
+D2Q21, D2Q49 = 21, 49
 PERIODIC = 0
 ZERO_GRADIENT = 1
 
@@ -30,7 +33,7 @@ class Config(ctypes.Structure):
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("overlap", ctypes.c_double), ("overlap_rule", ctypes.c_int),
-        ("moments", ctypes.c_int),
+        ("moments", ctypes.c_int), ("prandtl", ctypes.c_double), ("stencil", ctypes.c_int),
     ]
 
 
@@ -51,7 +54,12 @@ def lib():
     global _lib
     if _lib is None:
         L = ctypes.CDLL(_build.build())
-        L.ora_velocities.argtypes = [np.ctypeslib.ndpointer(np.int32), np.ctypeslib.ndpointer(np.int32)]
+        L.ora_velocities.argtypes = [ctypes.c_int, np.ctypeslib.ndpointer(np.int32),
+                                     np.ctypeslib.ndpointer(np.int32)]
+        L.ora_equilibrium13.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp,
+                                                                ctypes.POINTER(ctypes.c_int)]
+        L.ora_equilibrium13.restype = ctypes.c_int
+        L.ora_targets13.argtypes = [ctypes.c_double] * 4 + [_dp]
         L.ora_equilibrium.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp,
                                                               ctypes.POINTER(ctypes.c_int)]
         L.ora_equilibrium.restype = ctypes.c_int
@@ -67,13 +75,16 @@ def lib():
         L.ora_select_shift_neighbours.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_int]
         L.ora_select_shift_neighbours.restype = ctypes.c_int
-        L.ora_node_moments.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
+        L.ora_node_moments.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, _dp]
         L.ora_collide_node.argtypes = [ctypes.POINTER(Config), _dp, _dp, ctypes.c_int, ctypes.c_int,
                                        _dp, _dp]
         L.ora_collide_node.restype = ctypes.c_int
         L.ora_grad_populations.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.c_int] + \
-            [ctypes.c_double] * 4 + [_dp, _dp, ctypes.c_double, _dp, _dp]
+            [ctypes.c_double] * 4 + [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.ora_grad_populations.restype = ctypes.c_int
+        L.ora_heat_flux.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, _dp]
         L.ora_create.argtypes = [ctypes.POINTER(Config)]
         L.ora_create.restype = ctypes.c_void_p
         L.ora_destroy.argtypes = [ctypes.c_void_p]
@@ -95,7 +106,8 @@ def lib():
 
 def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=PERIODIC,
                 sensor=False, sensor_eps=(0.01, 0.1, 1.0), sensor_alpha=(1.05, 1.35, 1.6),
-                newton_tol=1e-12, newton_maxit=50, overlap=0.0, overlap_rule=0, moments=8):
+                newton_tol=1e-12, newton_maxit=50, overlap=0.0, overlap_rule=0, moments=None,
+                prandtl=1.0, stencil=D2Q21):
     c = Config()
     c.nx, c.ny, c.umax = nx, ny, umax
     c.nu, c.gamma, c.n0 = nu, gamma, n0
@@ -106,15 +118,34 @@ def make_config(nx, ny, umax=2, nu=1e-3, gamma=1.4, n0=0.5, bc_x=PERIODIC, bc_y=
     c.newton_tol, c.newton_maxit = newton_tol, newton_maxit
     c.overlap = overlap
     c.overlap_rule = overlap_rule
-    c.moments = moments
+    c.moments = (13 if stencil == D2Q49 else 8) if moments is None else moments
+    c.prandtl = prandtl
+    c.stencil = stencil
     return c
 
 
-def velocities():
-    x = np.zeros(Q, np.int32)
-    y = np.zeros(Q, np.int32)
-    lib().ora_velocities(x, y)
+def velocities(stencil=D2Q21):
+    n = Q49 if stencil == D2Q49 else Q
+    x = np.zeros(n, np.int32)
+    y = np.zeros(n, np.int32)
+    lib().ora_velocities(stencil, x, y)
     return x, y
+
+
+def equilibrium13(rho, ubx, uby, T, tol=1e-12, maxit=50):
+    """The reference solver's 13-moment equilibrium on D2Q49 (App. C.1);
+    returns (status, lambda, feq, iters)."""
+    lam = np.zeros(M13)
+    feq = np.zeros(Q49)
+    it = ctypes.c_int(0)
+    st = lib().ora_equilibrium13(rho, ubx, uby, T, tol, maxit, lam, feq, ctypes.byref(it))
+    return st, lam, feq, it.value
+
+
+def targets13(rho, ubx, uby, T):
+    m = np.zeros(M13)
+    lib().ora_targets13(rho, ubx, uby, T, m)
+    return m
 
 
 def equilibrium(rho, ubx, uby, T, tol=1e-12, maxit=50):
@@ -160,26 +191,38 @@ def select_shift_kept(u, current, w, n0=0.5, umax=2):
 
 def node_moments(f, g, Ux, Uy, gamma=1.4):
     out = np.zeros(4)
-    lib().ora_node_moments(np.ascontiguousarray(f, np.float64), np.ascontiguousarray(g, np.float64),
-                           int(Ux), int(Uy), gamma, out)
+    lib().ora_node_moments(len(f), np.ascontiguousarray(f, np.float64),
+                           np.ascontiguousarray(g, np.float64), int(Ux), int(Uy), gamma, out)
     return out
 
 
+def _q(cfg):
+    return Q49 if cfg.stencil == D2Q49 else Q
+
+
 def collide_node(cfg, f, g, Ux, Uy):
-    fs = np.zeros(Q)
-    gs = np.zeros(Q)
+    fs = np.zeros(_q(cfg))
+    gs = np.zeros(_q(cfg))
     st = lib().ora_collide_node(ctypes.byref(cfg), np.ascontiguousarray(f, np.float64),
                                 np.ascontiguousarray(g, np.float64), int(Ux), int(Uy), fs, gs)
     return st, fs, gs
 
 
-def grad_populations(cfg, Ux, Uy, rho, ux, uy, T, du, dT, omega):
-    f = np.zeros(Q)
-    g = np.zeros(Q)
+def grad_populations(cfg, Ux, Uy, rho, ux, uy, T, du, dT, omega, w_pr=0.0):
+    f = np.zeros(_q(cfg))
+    g = np.zeros(_q(cfg))
     st = lib().ora_grad_populations(ctypes.byref(cfg), int(Ux), int(Uy), rho, ux, uy, T,
                                     np.ascontiguousarray(du, np.float64).reshape(4),
-                                    np.ascontiguousarray(dT, np.float64), omega, f, g)
+                                    np.ascontiguousarray(dT, np.float64), omega, w_pr, f, g)
     return st, f, g
+
+
+def heat_flux(f, g, Ux, Uy, ux, uy):
+    q = np.zeros(2)
+    lib().ora_heat_flux(len(f), np.ascontiguousarray(f, np.float64),
+                        np.ascontiguousarray(g, np.float64), int(Ux), int(Uy), float(ux), float(uy),
+                        q)
+    return q
 
 
 class Simulation:
@@ -230,11 +273,11 @@ class Simulation:
         return ux.reshape(self.ny, self.nx), uy.reshape(self.ny, self.nx)
 
     def populations(self):
-        n = self.nx * self.ny
-        f = np.zeros(n * Q)
-        g = np.zeros(n * Q)
+        n, q = self.nx * self.ny, _q(self.cfg)
+        f = np.zeros(n * q)
+        g = np.zeros(n * q)
         lib().ora_get_populations(self._h, f, g)
-        return f.reshape(self.ny, self.nx, Q), g.reshape(self.ny, self.nx, Q)
+        return f.reshape(self.ny, self.nx, q), g.reshape(self.ny, self.nx, q)
 
     def set_state(self, f, g, ux, uy):
         lib().ora_set_state(self._h, np.ascontiguousarray(f, np.float64).reshape(-1),

@@ -25,11 +25,23 @@ static const int XI[ORA_Q][2] = {
     {3, 0},  {0, 3},  {-3, 0},  {0, -3},
 };
 
+/* D2Q49: every integer velocity in {-3..3}^2, index (x + 3) + 7 (y + 3); the
+ * lattice of the paper's reference solver (Sec. IV.B, App. C.1). */
+#define ROW49(y) {-3, y}, {-2, y}, {-1, y}, {0, y}, {1, y}, {2, y}, {3, y}
+static const int XI49[ORA_Q49][2] = {ROW49(-3), ROW49(-2), ROW49(-1), ROW49(0),
+                                     ROW49(1),  ROW49(2),  ROW49(3)};
+#undef ROW49
+
+/* Velocity table of a stencil (Q = 21 or 49). */
+static const int (*stencil_xi(int Q))[2] { return Q == ORA_Q49 ? XI49 : XI; }
+
 static const double D_SPACE = 2.0; /* D = 2 spatial dimensions (Sec. C.1) */
 
 struct ora_state {
   ora_config cfg;
   int n;
+  int Q;                /* populations per node: 21 or 49 */
+  const int (*xi)[2];   /* their velocities */
   double *f, *g;        /* pre-collision populations [node][i] */
   double *fs, *gs;      /* post-collision populations [node][i] */
   signed char *Ux, *Uy; /* lattice of f, g */
@@ -38,10 +50,12 @@ struct ora_state {
   ora_stats stats;
 };
 
-void ora_velocities(int xi_x[ORA_Q], int xi_y[ORA_Q]) {
-  for (int i = 0; i < ORA_Q; ++i) {
-    xi_x[i] = XI[i][0];
-    xi_y[i] = XI[i][1];
+void ora_velocities(int stencil, int* xi_x, int* xi_y) {
+  const int Q = stencil == ORA_D2Q49 ? ORA_Q49 : ORA_Q;
+  const int(*xi)[2] = stencil_xi(Q);
+  for (int i = 0; i < Q; ++i) {
+    xi_x[i] = xi[i][0];
+    xi_y[i] = xi[i][1];
   }
 }
 
@@ -315,6 +329,159 @@ int ora_equilibrium4(double rho, double ubx, double uby, double T, double tol, i
   return status;
 }
 
+/* ------------------------------------------------------------------------- */
+/* The reference solver's equilibrium (App. C.1) on D2Q49. */
+
+/* Monomials of Eq. feqNum_13Mom. The printed exponent lists nine of the ten
+ * monomials up to third order (lambda_3,xxx x^3 is missing) for thirteen
+ * constraints; the square system needs all of them, so x^3 is included. */
+static void monomials13(double x, double y, double P[ORA_M13]) {
+  const double r2 = x * x + y * y;
+  P[0] = 1.0;
+  P[1] = x;
+  P[2] = y;
+  P[3] = x * x;
+  P[4] = x * y;
+  P[5] = y * y;
+  P[6] = x * x * x;
+  P[7] = x * x * y;
+  P[8] = x * y * y;
+  P[9] = y * y * y;
+  P[10] = x * x * r2;
+  P[11] = x * y * r2;
+  P[12] = y * y * r2;
+}
+
+/* Eqs. G0..G4yyaa in the lattice frame, 2E = |u|^2 + D T. */
+void ora_targets13(double rho, double ubx, double uby, double T, double m[ORA_M13]) {
+  const double E = 0.5 * (ubx * ubx + uby * uby + D_SPACE * T);
+  m[0] = rho;
+  m[1] = rho * ubx;
+  m[2] = rho * uby;
+  m[3] = rho * (ubx * ubx + T);
+  m[4] = rho * ubx * uby;
+  m[5] = rho * (uby * uby + T);
+  m[6] = rho * ubx * (ubx * ubx + 3.0 * T);
+  m[7] = rho * (ubx * ubx + T) * uby;
+  m[8] = rho * ubx * (uby * uby + T);
+  m[9] = rho * uby * (uby * uby + 3.0 * T);
+  m[10] = 2.0 * rho * ((E + 2.0 * T) * ubx * ubx + (E + T) * T);
+  m[11] = 2.0 * rho * ((E + 2.0 * T) * ubx * uby);
+  m[12] = 2.0 * rho * ((E + 2.0 * T) * uby * uby + (E + T) * T);
+}
+
+static void exp_family13(const double l[ORA_M13], double p[ORA_Q49]) {
+  for (int i = 0; i < ORA_Q49; ++i) {
+    double P[ORA_M13];
+    monomials13(XI49[i][0], XI49[i][1], P);
+    double s = 1.0;
+    for (int k = 0; k < ORA_M13; ++k) s += l[k] * P[k];
+    p[i] = exp(-s);
+  }
+}
+
+static double dual_value13(const double l[ORA_M13], const double p[ORA_Q49],
+                           const double m[ORA_M13]) {
+  double F = 0.0;
+  for (int i = 0; i < ORA_Q49; ++i) F += p[i];
+  for (int k = 0; k < ORA_M13; ++k) F += l[k] * m[k];
+  return F;
+}
+
+/* Cholesky solve of an n x n symmetric positive definite system (row-major A). */
+static int cholesky_solve_n(int n, const double* A, const double* b, double* x) {
+  double L[ORA_M13 * ORA_M13], y[ORA_M13];
+  memset(L, 0, sizeof(L));
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0) || !isfinite(d)) return ORA_ESINGULAR;
+    L[j * n + j] = sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = t / L[j * n + j];
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = b[i];
+    for (int k = 0; k < i; ++k) t -= L[i * n + k] * y[k];
+    y[i] = t / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * x[k];
+    x[i] = t / L[i * n + i];
+  }
+  return ORA_OK;
+}
+
+int ora_equilibrium13(double rho, double ubx, double uby, double T, double tol, int maxit,
+                      double lambda[ORA_M13], double feq[ORA_Q49], int* iters) {
+  *iters = 0;
+  if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ubx) ||
+      !isfinite(uby))
+    return ORA_EUNREALIZABLE;
+  double m[ORA_M13];
+  ora_targets13(rho, ubx, uby, T, m);
+  for (int k = 0; k < ORA_M13; ++k) m[k] /= rho;
+  /* Maxwellian start: lambda_1 = -ubar/T, lambda_2aa = 1/(2T), lambda_0 from
+   * the normalisation, the rest 0 */
+  for (int k = 0; k < ORA_M13; ++k) lambda[k] = 0.0;
+  lambda[1] = -ubx / T;
+  lambda[2] = -uby / T;
+  lambda[3] = 0.5 / T;
+  lambda[5] = 0.5 / T;
+  double p[ORA_Q49];
+  exp_family13(lambda, p);
+  double Z = 0.0;
+  for (int i = 0; i < ORA_Q49; ++i) Z += p[i];
+  lambda[0] = log(Z);
+  exp_family13(lambda, p);
+  double F = dual_value13(lambda, p, m);
+  int status = ORA_ENEWTON;
+  int it = 0;
+  for (;;) {
+    double G[ORA_M13], H[ORA_M13 * ORA_M13];
+    for (int k = 0; k < ORA_M13; ++k) G[k] = -m[k];
+    memset(H, 0, sizeof(H));
+    for (int i = 0; i < ORA_Q49; ++i) {
+      double P[ORA_M13];
+      monomials13(XI49[i][0], XI49[i][1], P);
+      for (int a = 0; a < ORA_M13; ++a) {
+        G[a] += p[i] * P[a];
+        for (int b = 0; b < ORA_M13; ++b) H[a * ORA_M13 + b] += p[i] * P[a] * P[b];
+      }
+    }
+    double gmax = 0.0;
+    for (int k = 0; k < ORA_M13; ++k) gmax = fmax(gmax, fabs(G[k]));
+    if (!isfinite(gmax)) { status = ORA_ESINGULAR; break; }
+    if (gmax <= tol) { status = ORA_OK; break; }
+    if (it >= maxit) { status = ORA_ENEWTON; break; }
+    double d[ORA_M13];
+    if (cholesky_solve_n(ORA_M13, H, G, d) != ORA_OK) { status = ORA_ESINGULAR; break; }
+    double gd = 0.0;
+    for (int k = 0; k < ORA_M13; ++k) gd += G[k] * d[k];
+    double t = 1.0, lam_c[ORA_M13], p_c[ORA_Q49], F_c = 0.0;
+    int accepted = 0;
+    for (int ls = 0; ls < 40; ++ls) {
+      for (int k = 0; k < ORA_M13; ++k) lam_c[k] = lambda[k] + t * d[k];
+      exp_family13(lam_c, p_c);
+      F_c = dual_value13(lam_c, p_c, m);
+      if (isfinite(F_c) && F_c <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) { accepted = 1; break; }
+      t *= 0.5;
+    }
+    ++it;
+    if (!accepted) { status = ORA_ENEWTON; break; }
+    for (int k = 0; k < ORA_M13; ++k) lambda[k] = lam_c[k];
+    for (int i = 0; i < ORA_Q49; ++i) p[i] = p_c[i];
+    F = F_c;
+  }
+  *iters = it;
+  for (int i = 0; i < ORA_Q49; ++i) feq[i] = rho * p[i];
+  return status;
+}
+
 /* Eq. criterion: U_a = n iff n - 0.5 < u_a <= n + 0.5. With an offset n0 the
  * interval is read as (n - n0, n + 1 - n0]; shifts are clamped to [-umax, umax]. */
 int ora_select_shift(double u, double n0, int umax) {
@@ -370,12 +537,13 @@ int ora_select_shift_neighbours(double u, double n0, int umax, double w, const i
  * rho = sum f, rho u = sum f c, and T = [sum(|c|^2 f + g) - rho |u|^2] / (2 rho Cv).
  * Summing in the lattice frame (xi instead of c) gives the same T exactly in
  * exact arithmetic; the lattice frame is used so that results do not depend on U. */
-void ora_node_moments(const double f[ORA_Q], const double g[ORA_Q], int Ux, int Uy,
-                      double gamma, double out[4]) {
+void ora_node_moments(int Q, const double* f, const double* g, int Ux, int Uy, double gamma,
+                      double out[4]) {
+  const int(*xi)[2] = stencil_xi(Q);
   const double Cv = 1.0 / (gamma - 1.0);
   double rho = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
-  for (int i = 0; i < ORA_Q; ++i) {
-    const double x = XI[i][0], y = XI[i][1];
+  for (int i = 0; i < Q; ++i) {
+    const double x = xi[i][0], y = xi[i][1];
     rho += f[i];
     jx += f[i] * x;
     jy += f[i] * y;
@@ -408,8 +576,12 @@ static double sensor_alpha(const ora_config* c, double eps) {
 
 /* Numerical equilibrium of the configured constraint set (8 or 4 moments). */
 static int equilibrium_cfg(const ora_config* c, double rho, double ubx, double uby, double T,
-                           double feq[ORA_Q]) {
+                           double* feq) {
   int iters;
+  if (c->stencil == ORA_D2Q49) {
+    double l13[ORA_M13];
+    return ora_equilibrium13(rho, ubx, uby, T, c->newton_tol, c->newton_maxit, l13, feq, &iters);
+  }
   if (c->moments == 4) {
     double l4[4];
     return ora_equilibrium4(rho, ubx, uby, T, c->newton_tol, c->newton_maxit, l4, feq, &iters);
@@ -418,49 +590,90 @@ static int equilibrium_cfg(const ora_config* c, double rho, double ubx, double u
   return ora_equilibrium(rho, ubx, uby, T, c->newton_tol, c->newton_maxit, lambda, feq, &iters);
 }
 
-/* Collision of one node (Eqs. coll, gEq, DeltaAvg) in its own lattice U. */
-int ora_collide_node(const ora_config* cfg, const double f[ORA_Q], const double g[ORA_Q],
-                     int Ux, int Uy, double fs[ORA_Q], double gs[ORA_Q]) {
+void ora_heat_flux(int Q, const double* f, const double* g, int Ux, int Uy, double ux,
+                   double uy, double q[2]) {
+  const int(*xi)[2] = stencil_xi(Q);
+  q[0] = q[1] = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    const double cx = (double)(xi[i][0] + Ux) - ux;
+    const double cy = (double)(xi[i][1] + Uy) - uy;
+    const double e = (cx * cx + cy * cy) * f[i] + g[i];
+    q[0] += 0.5 * cx * e;
+    q[1] += 0.5 * cy * e;
+  }
+}
+
+/* Collision of one node (Eqs. coll, gEq, DeltaAvg) in its own lattice U; for
+ * Pr != 1 the heat-flux term of Eqs. Shakhov / prandtlPoly is added:
+ *   f* += (1/tau - 1/tau_Pr) q.cbar / (rho Cp T^2) (|cbar|^2 / (2T) - Cp) f^eq,
+ *   g* += (1/tau - 1/tau_Pr) 2 q.cbar / (rho Cp) g^eq,
+ * with tau_Pr = 1/2 + (nu/Pr)/T; the sensor factor scales tau and tau_Pr alike. */
+int ora_collide_node(const ora_config* cfg, const double* f, const double* g, int Ux, int Uy,
+                     double* fs, double* gs) {
+  const int Q = cfg->stencil == ORA_D2Q49 ? ORA_Q49 : ORA_Q;
+  const int(*xi)[2] = stencil_xi(Q);
   double mom[4];
-  ora_node_moments(f, g, Ux, Uy, cfg->gamma, mom);
+  ora_node_moments(Q, f, g, Ux, Uy, cfg->gamma, mom);
   const double rho = mom[0], T = mom[3];
-  double feq[ORA_Q];
+  double feq[ORA_QMAX];
   int st = equilibrium_cfg(cfg, rho, mom[1] - Ux, mom[2] - Uy, T, feq);
   if (st != ORA_OK) {
     /* failure policy: the node is left uncollided */
-    for (int i = 0; i < ORA_Q; ++i) { fs[i] = f[i]; gs[i] = g[i]; }
+    for (int i = 0; i < Q; ++i) { fs[i] = f[i]; gs[i] = g[i]; }
     return st;
   }
   const double Cv = 1.0 / (cfg->gamma - 1.0);
+  const double Cp = cfg->gamma * Cv;
   double tau = 0.5 + cfg->nu / T;
+  double tau_pr = 0.5 + (cfg->nu / cfg->prandtl) / T;
   if (cfg->sensor) {
     double eps = 0.0;
-    for (int i = 0; i < ORA_Q; ++i) eps += fabs(f[i] - feq[i]) / feq[i];
-    eps /= (double)ORA_Q;
-    tau *= sensor_alpha(cfg, eps);
+    for (int i = 0; i < Q; ++i) eps += fabs(f[i] - feq[i]) / feq[i];
+    eps /= (double)Q;
+    const double a = sensor_alpha(cfg, eps);
+    tau *= a;
+    tau_pr *= a;
   }
-  for (int i = 0; i < ORA_Q; ++i) {
+  for (int i = 0; i < Q; ++i) {
     const double geq = (2.0 * Cv - D_SPACE) * T * feq[i];
     fs[i] = f[i] - (f[i] - feq[i]) / tau;
     gs[i] = g[i] - (g[i] - geq) / tau;
+  }
+  if (cfg->prandtl != 1.0) {
+    double q[2];
+    ora_heat_flux(Q, f, g, Ux, Uy, mom[1], mom[2], q);
+    const double w = 1.0 / tau - 1.0 / tau_pr;
+    for (int i = 0; i < Q; ++i) {
+      const double cx = (double)(xi[i][0] + Ux) - mom[1];
+      const double cy = (double)(xi[i][1] + Uy) - mom[2];
+      const double c2 = cx * cx + cy * cy;
+      const double qc = q[0] * cx + q[1] * cy;
+      const double geq = (2.0 * Cv - D_SPACE) * T * feq[i];
+      fs[i] += w * qc / (rho * Cp * T * T) * (c2 / (2.0 * T) - Cp) * feq[i];
+      gs[i] += w * 2.0 * qc / (rho * Cp) * geq;
+    }
   }
   return ORA_OK;
 }
 
 /* Grad's approximation h = h^eq (1 + omega phi_h): Eq. GradGeneral with phi_f
  * from Eq. GradGeneral_f (traceless viscous stress, Fourier heat flux, mu = rho nu,
- * kappa = rho Cp nu for Pr = 1) and phi_g from Eq. GradGeneral_g, both as printed.
- * cbar = c_i - u with c_i = xi_i + U. */
+ * kappa = rho Cp nu / Pr, Pr = 1 for BGK) and phi_g from Eq. GradGeneral_g, both
+ * as printed. cbar = c_i - u with c_i = xi_i + U. The heat-flux part of phi_f
+ * has the shape of the App. E term, so the collision of App. E applied to the
+ * Grad population (with q its Fourier flux) adds w_pr times that part. */
 int ora_grad_populations(const ora_config* cfg, int Ux, int Uy, double rho, double ux,
                          double uy, double T, const double du[2][2], const double dT[2],
-                         double omega, double f[ORA_Q], double g[ORA_Q]) {
+                         double omega, double w_pr, double* f, double* g) {
+  const int Q = cfg->stencil == ORA_D2Q49 ? ORA_Q49 : ORA_Q;
+  const int(*xi)[2] = stencil_xi(Q);
   const double Cv = 1.0 / (cfg->gamma - 1.0);
   const double Cp = cfg->gamma * Cv;
-  double feq[ORA_Q];
+  double feq[ORA_QMAX];
   int st = equilibrium_cfg(cfg, rho, ux - Ux, uy - Uy, T, feq);
   if (st != ORA_OK) return st;
   const double mu = rho * cfg->nu;
-  const double kappa = rho * Cp * cfg->nu;
+  const double kappa = rho * Cp * cfg->nu / cfg->prandtl;
   /* -sigma_ab = mu [d_a u_b + d_b u_a - (2/D) d_c u_c delta_ab] */
   const double div = du[0][0] + du[1][1];
   const double sxx = -mu * (2.0 * du[0][0] - (2.0 / D_SPACE) * div);
@@ -468,17 +681,18 @@ int ora_grad_populations(const ora_config* cfg, int Ux, int Uy, double rho, doub
   const double sxy = -mu * (du[0][1] + du[1][0]);
   const double qx = -kappa * dT[0];
   const double qy = -kappa * dT[1];
-  for (int i = 0; i < ORA_Q; ++i) {
-    const double cx = (double)(XI[i][0] + Ux) - ux;
-    const double cy = (double)(XI[i][1] + Uy) - uy;
+  for (int i = 0; i < Q; ++i) {
+    const double cx = (double)(xi[i][0] + Ux) - ux;
+    const double cy = (double)(xi[i][1] + Uy) - uy;
     const double c2 = cx * cx + cy * cy;
     const double qc = qx * cx + qy * cy;
-    const double phi_f = (sxx * cx * cx + 2.0 * sxy * cx * cy + syy * cy * cy) / (2.0 * rho * T * T) +
-                         qc / (rho * Cp * T * T) * (c2 / (2.0 * T) - Cp);
+    const double phi_s = (sxx * cx * cx + 2.0 * sxy * cx * cy + syy * cy * cy) / (2.0 * rho * T * T);
+    const double phi_q = qc / (rho * Cp * T * T) * (c2 / (2.0 * T) - Cp);
+    const double phi_f = phi_s + phi_q;
     const double phi_g = 2.0 * qc / (rho * Cp);
     const double geq = (2.0 * Cv - D_SPACE) * T * feq[i];
-    f[i] = feq[i] * (1.0 + omega * phi_f);
-    g[i] = geq * (1.0 + omega * phi_g);
+    f[i] = feq[i] * (1.0 + omega * phi_f + w_pr * phi_q);
+    g[i] = geq * (1.0 + omega * phi_g + w_pr * phi_g);
   }
   return ORA_OK;
 }
@@ -523,12 +737,21 @@ ora_state* ora_create(const ora_config* cfg) {
   if (!(cfg->overlap >= 0.0 && cfg->overlap <= 1.0)) return NULL;
   if (cfg->overlap_rule != ORA_RULE_HISTORY && cfg->overlap_rule != ORA_RULE_NEIGHBOURS)
     return NULL;
-  if (cfg->moments != 8 && cfg->moments != 4) return NULL;
+  if (!(cfg->prandtl > 0.0)) return NULL;
+  if (cfg->stencil == ORA_D2Q21) {
+    if (cfg->moments != 8 && cfg->moments != 4) return NULL;
+  } else if (cfg->stencil == ORA_D2Q49) {
+    if (cfg->moments != 13) return NULL;
+  } else {
+    return NULL;
+  }
   ora_state* s = (ora_state*)calloc(1, sizeof(ora_state));
   if (!s) return NULL;
   s->cfg = *cfg;
   s->n = cfg->nx * cfg->ny;
-  const size_t nq = (size_t)s->n * ORA_Q;
+  s->Q = cfg->stencil == ORA_D2Q49 ? ORA_Q49 : ORA_Q;
+  s->xi = stencil_xi(s->Q);
+  const size_t nq = (size_t)s->n * s->Q;
   s->f = (double*)calloc(nq, sizeof(double));
   s->g = (double*)calloc(nq, sizeof(double));
   s->fs = (double*)calloc(nq, sizeof(double));
@@ -587,7 +810,7 @@ int ora_init(ora_state* s, const double* rho, const double* rhoux, const double*
       du[0][0] = dux[0]; du[1][0] = dux[1]; /* du[a][b] = d_a u_b */
       du[0][1] = duy[0]; du[1][1] = duy[1];
       int st = ora_grad_populations(c, Ux, Uy, s->rho[k], s->ux[k], s->uy[k], s->T[k], du, dT,
-                                    1.0, &s->f[(size_t)k * ORA_Q], &s->g[(size_t)k * ORA_Q]);
+                                    1.0, 0.0, &s->f[(size_t)k * s->Q], &s->g[(size_t)k * s->Q]);
       if (st != ORA_OK) status = st;
       s->Ux[k] = (signed char)Ux;
       s->Uy[k] = (signed char)Uy;
@@ -613,9 +836,10 @@ static int rebuild_pull(ora_state* s, int i, int Upx, int Upy, int sx, int sy, d
   du[0][0] = dux[0]; du[1][0] = dux[1];
   du[0][1] = duy[0]; du[1][1] = duy[1];
   const double tau = 0.5 + c->nu / s->T[k];
-  double f[ORA_Q], g[ORA_Q];
+  const double tau_pr = 0.5 + (c->nu / c->prandtl) / s->T[k];
+  double f[ORA_QMAX], g[ORA_QMAX];
   int st = ora_grad_populations(c, Upx, Upy, s->rho[k], s->ux[k], s->uy[k], s->T[k], du, dT,
-                                1.0 - 1.0 / tau, f, g);
+                                1.0 - 1.0 / tau, 1.0 / tau - 1.0 / tau_pr, f, g);
   if (st != ORA_OK) return st;
   *fi = f[i];
   *gi = g[i];
@@ -623,18 +847,31 @@ static int rebuild_pull(ora_state* s, int i, int Upx, int Upy, int sx, int sy, d
 }
 
 /* Fallback for a rebuild whose root finder failed: the Maxwellian-guess
- * exponential (always positive) of the sender's state in the receiver's lattice. */
+ * exponential (always positive) of the sender's state in the receiver's lattice,
+ * rho exp(-|xi - ubar|^2 / (2T)) normalised over the lattice. */
 static void rebuild_fallback(ora_state* s, int i, int Upx, int Upy, int sx, int sy, double* fi,
                              double* gi) {
   const ora_config* c = &s->cfg;
   int gx, gy;
   const int k = resolve(sy, c->ny, c->bc_y, &gy) * c->nx + resolve(sx, c->nx, c->bc_x, &gx);
   const double Cv = 1.0 / (c->gamma - 1.0);
-  double lambda[ORA_M], p[ORA_Q];
-  maxwellian_guess(s->ux[k] - Upx, s->uy[k] - Upy, s->T[k], lambda);
-  exp_family(lambda, p);
-  *fi = s->rho[k] * p[i];
-  *gi = (2.0 * Cv - D_SPACE) * s->T[k] * (*fi);
+  const double ubx = s->ux[k] - Upx, uby = s->uy[k] - Upy, T = s->T[k];
+  if (s->Q == ORA_Q) {
+    double lambda[ORA_M], p[ORA_Q];
+    maxwellian_guess(ubx, uby, T, lambda);
+    exp_family(lambda, p);
+    *fi = s->rho[k] * p[i];
+  } else {
+    double Z = 0.0, pi = 0.0;
+    for (int j = 0; j < s->Q; ++j) {
+      const double dx = s->xi[j][0] - ubx, dy = s->xi[j][1] - uby;
+      const double e = exp(-(dx * dx + dy * dy) / (2.0 * T));
+      Z += e;
+      if (j == i) pi = e;
+    }
+    *fi = s->rho[k] * pi / Z;
+  }
+  *gi = (2.0 * Cv - D_SPACE) * T * (*fi);
 }
 
 /* One time iteration; if forced_x / forced_y are given they replace the
@@ -642,19 +879,21 @@ static void rebuild_fallback(ora_state* s, int i, int Upx, int Upy, int sx, int 
 static int step_once(ora_state* s, const signed char* forced_x, const signed char* forced_y) {
   const ora_config* c = &s->cfg;
   const int nx = c->nx, ny = c->ny;
+  const int Q = s->Q;
+  const int(*xi)[2] = s->xi;
   int status = ORA_OK;
   {
     /* (i) moments, equilibrium, collision, next shift: every node in its own lattice */
     long long fails = 0, calls = 0;
 #pragma omp parallel for reduction(+ : fails, calls) schedule(static)
     for (int k = 0; k < s->n; ++k) {
-      const double* f = &s->f[(size_t)k * ORA_Q];
-      const double* g = &s->g[(size_t)k * ORA_Q];
+      const double* f = &s->f[(size_t)k * Q];
+      const double* g = &s->g[(size_t)k * Q];
       double mom[4];
-      ora_node_moments(f, g, s->Ux[k], s->Uy[k], c->gamma, mom);
+      ora_node_moments(Q, f, g, s->Ux[k], s->Uy[k], c->gamma, mom);
       s->rho[k] = mom[0]; s->ux[k] = mom[1]; s->uy[k] = mom[2]; s->T[k] = mom[3];
-      int st = ora_collide_node(c, f, g, s->Ux[k], s->Uy[k], &s->fs[(size_t)k * ORA_Q],
-                                &s->gs[(size_t)k * ORA_Q]);
+      int st = ora_collide_node(c, f, g, s->Ux[k], s->Uy[k], &s->fs[(size_t)k * Q],
+                                &s->gs[(size_t)k * Q]);
       calls += 1;
       if (st != ORA_OK) fails += 1;
       if (forced_x) {
@@ -694,17 +933,17 @@ static int step_once(ora_state* s, const signed char* forced_x, const signed cha
     for (int k = 0; k < s->n; ++k) {
       const int x = k % nx, y = k / nx;
       const int Upx = s->Unx[k], Upy = s->Uny[k];
-      for (int i = 0; i < ORA_Q; ++i) {
-        const int sx = x - (XI[i][0] + Upx);
-        const int sy = y - (XI[i][1] + Upy);
+      for (int i = 0; i < Q; ++i) {
+        const int sx = x - (xi[i][0] + Upx);
+        const int sy = y - (xi[i][1] + Upy);
         int gx, gy;
         const int rx = resolve(sx, nx, c->bc_x, &gx);
         const int ry = resolve(sy, ny, c->bc_y, &gy);
         const int ks = ry * nx + rx;
         double fi, gi;
         if (!gx && !gy && s->Ux[ks] == Upx && s->Uy[ks] == Upy) {
-          fi = s->fs[(size_t)ks * ORA_Q + i];
-          gi = s->gs[(size_t)ks * ORA_Q + i];
+          fi = s->fs[(size_t)ks * Q + i];
+          gi = s->gs[(size_t)ks * Q + i];
         } else {
           rec += 1;
           if (rebuild_pull(s, i, Upx, Upy, sx, sy, &fi, &gi) != ORA_OK) {
@@ -712,8 +951,8 @@ static int step_once(ora_state* s, const signed char* forced_x, const signed cha
             rebuild_fallback(s, i, Upx, Upy, sx, sy, &fi, &gi);
           }
         }
-        s->f[(size_t)k * ORA_Q + i] = fi;
-        s->g[(size_t)k * ORA_Q + i] = gi;
+        s->f[(size_t)k * Q + i] = fi;
+        s->g[(size_t)k * Q + i] = gi;
       }
     }
     s->stats.reconstructions += rec;
@@ -747,8 +986,8 @@ int ora_step_forced(ora_state* s, const signed char* ux, const signed char* uy) 
 void ora_get_primitives(const ora_state* s, double* rho, double* ux, double* uy, double* T) {
   for (int k = 0; k < s->n; ++k) {
     double mom[4];
-    ora_node_moments(&s->f[(size_t)k * ORA_Q], &s->g[(size_t)k * ORA_Q], s->Ux[k], s->Uy[k],
-                     s->cfg.gamma, mom);
+    ora_node_moments(s->Q, &s->f[(size_t)k * s->Q], &s->g[(size_t)k * s->Q], s->Ux[k],
+                     s->Uy[k], s->cfg.gamma, mom);
     rho[k] = mom[0]; ux[k] = mom[1]; uy[k] = mom[2]; T[k] = mom[3];
   }
 }
@@ -758,8 +997,8 @@ void ora_get_moments(const ora_state* s, double* rho, double* rhoux, double* rho
   const double Cv = 1.0 / (s->cfg.gamma - 1.0);
   for (int k = 0; k < s->n; ++k) {
     double mom[4];
-    ora_node_moments(&s->f[(size_t)k * ORA_Q], &s->g[(size_t)k * ORA_Q], s->Ux[k], s->Uy[k],
-                     s->cfg.gamma, mom);
+    ora_node_moments(s->Q, &s->f[(size_t)k * s->Q], &s->g[(size_t)k * s->Q], s->Ux[k],
+                     s->Uy[k], s->cfg.gamma, mom);
     const double r = mom[0], ux = mom[1], uy = mom[2], T = mom[3];
     rho[k] = r;
     rhoux[k] = r * ux;
@@ -774,14 +1013,14 @@ void ora_get_shifts(const ora_state* s, signed char* ux, signed char* uy) {
 }
 
 void ora_get_populations(const ora_state* s, double* f, double* g) {
-  memcpy(f, s->f, sizeof(double) * (size_t)s->n * ORA_Q);
-  memcpy(g, s->g, sizeof(double) * (size_t)s->n * ORA_Q);
+  memcpy(f, s->f, sizeof(double) * (size_t)s->n * s->Q);
+  memcpy(g, s->g, sizeof(double) * (size_t)s->n * s->Q);
 }
 
 void ora_set_state(ora_state* s, const double* f, const double* g, const signed char* ux,
                    const signed char* uy) {
-  memcpy(s->f, f, sizeof(double) * (size_t)s->n * ORA_Q);
-  memcpy(s->g, g, sizeof(double) * (size_t)s->n * ORA_Q);
+  memcpy(s->f, f, sizeof(double) * (size_t)s->n * s->Q);
+  memcpy(s->g, g, sizeof(double) * (size_t)s->n * s->Q);
   memcpy(s->Ux, ux, (size_t)s->n);
   memcpy(s->Uy, uy, (size_t)s->n);
 }

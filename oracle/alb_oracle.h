@@ -28,8 +28,17 @@
 extern "C" {
 #endif
 
-#define ORA_Q 21   /* D2Q21 */
-#define ORA_M 8    /* 8-moment constraint set */
+#define ORA_Q 21    /* D2Q21 */
+#define ORA_M 8     /* 8-moment constraint set */
+#define ORA_Q49 49  /* D2Q49, the reference solver's lattice (App. C.1) */
+#define ORA_M13 13  /* its 13-moment constraint set */
+#define ORA_QMAX 49
+
+/* Stencils (ora_config.stencil): the adaptive D2Q21 lattice, or the D2Q49
+ * lattice {-3..3}^2 with the 13-moment equilibrium of App. C.1 (Eqs. G0..G4yyaa,
+ * feqNum_13Mom) that the paper uses for its reference data. D2Q49 velocity
+ * i = (x, y) has index i = (x + 3) + 7 (y + 3). */
+enum { ORA_D2Q21 = 21, ORA_D2Q49 = 49 };
 
 enum { ORA_PERIODIC = 0, ORA_ZERO_GRADIENT = 1 };
 
@@ -59,6 +68,11 @@ typedef struct {
                           ORA_RULE_NEIGHBOURS takes the one most neighbours use */
   int moments;         /* constraint set of the equilibrium: 8 (Eqs. G0_8mom..G3yaa_8mom,
                           the default) or 4 (the reduced model, App. C.2) */
+  double prandtl;      /* Pr > 0. 1: BGK (Eq. coll). Otherwise the heat-flux
+                          corrected collision of App. E (Eqs. Shakhov, prandtlPoly)
+                          with tau_Pr = 1/2 + (nu/Pr)/T, and kappa = rho Cp nu / Pr in
+                          Grad's heat flux (Eq. GradGeneral_f) */
+  int stencil;         /* ORA_D2Q21, or ORA_D2Q49 with moments = 13 */
 } ora_config;
 
 enum { ORA_RULE_HISTORY = 0, ORA_RULE_NEIGHBOURS = 1 };
@@ -73,8 +87,9 @@ typedef struct {
 
 typedef struct ora_state ora_state;
 
-/* Velocity table, index order used everywhere in the oracle. */
-void ora_velocities(int xi_x[ORA_Q], int xi_y[ORA_Q]);
+/* Velocity table of a stencil (ORA_D2Q21 or ORA_D2Q49), in the index order used
+ * everywhere in the oracle. */
+void ora_velocities(int stencil, int* xi_x, int* xi_y);
 
 /* Numerical equilibrium (Eqs. exponential, feqNum_8Mom) in a lattice whose
  * populations move with xi_i + U: (rho, ubx, uby) is the velocity relative to U.
@@ -94,6 +109,18 @@ int ora_equilibrium4(double rho, double ubx, double uby, double T, double tol, i
 /* Constraint targets M_k(rho, ubar, T) of Eqs. G0_8mom..G3yaa_8mom. */
 void ora_targets(double rho, double ubx, double uby, double T, double m[ORA_M]);
 
+/* Reference solver's equilibrium on D2Q49 (App. C.1): the 13 constraints of
+ * Eqs. G0..G4yyaa (moments up to third order and the trace of the fourth,
+ * 2E = |ubar|^2 + D T) and the exponential family of Eq. feqNum_13Mom with the
+ * monomials (1, x, y, x^2, xy, y^2, x^3, x^2 y, x y^2, y^3, x^2 r^2, x y r^2,
+ * y^2 r^2), r^2 = x^2 + y^2, in that order for lambda. Same iteration and
+ * stopping rule as ora_equilibrium. */
+int ora_equilibrium13(double rho, double ubx, double uby, double T, double tol, int maxit,
+                      double lambda[ORA_M13], double feq[ORA_Q49], int* iters);
+
+/* Targets of Eqs. G0..G4yyaa in the monomial order of ora_equilibrium13. */
+void ora_targets13(double rho, double ubx, double uby, double T, double m[ORA_M13]);
+
 /* Shift criterion (Eq. criterion, with the n0 offset reading). */
 int ora_select_shift(double u, double n0, int umax);
 
@@ -110,23 +137,35 @@ int ora_select_shift_kept(double u, double n0, int umax, int current, double w);
  * examined in increasing n). */
 int ora_select_shift_neighbours(double u, double n0, int umax, double w, const int* nb, int nnb);
 
-/* Macroscopic moments of one node (Eq. polyTemp), populations in lattice U.
- * out = {rho, ux, uy, T} with u absolute (lattice-frame sums plus U). */
-void ora_node_moments(const double f[ORA_Q], const double g[ORA_Q], int Ux, int Uy,
-                      double gamma, double out[4]);
+/* Macroscopic moments of one node (Eq. polyTemp), Q = 21 or 49 populations in
+ * lattice U. out = {rho, ux, uy, T} with u absolute (lattice-frame sums plus U). */
+void ora_node_moments(int Q, const double* f, const double* g, int Ux, int Uy, double gamma,
+                      double out[4]);
 
-/* BGK collision of one node in its own lattice (Eqs. coll, gEq; optional
- * sensor). Returns ORA_OK or a Newton error (then fs, gs = f, g). */
-int ora_collide_node(const ora_config* cfg, const double f[ORA_Q], const double g[ORA_Q],
-                     int Ux, int Uy, double fs[ORA_Q], double gs[ORA_Q]);
+/* Collision of one node in its own lattice: BGK (Eqs. coll, gEq; optional
+ * sensor) and, for Pr != 1, the heat-flux term of Eqs. Shakhov / prandtlPoly
+ * with q the heat flux of the pre-collision populations (ora_heat_flux).
+ * Arrays hold cfg->stencil populations. Returns ORA_OK or a Newton error
+ * (then fs, gs = f, g). */
+int ora_collide_node(const ora_config* cfg, const double* f, const double* g, int Ux, int Uy,
+                     double* fs, double* gs);
 
-/* Grad populations h = h^eq (1 + omega * phi_h) in lattice (Ux, Uy) for the
- * macroscopic state (rho, ux, uy, T) with velocity gradients du[a][b] = d_a u_b
- * and temperature gradient dT[a] (Eqs. GradGeneral, GradGeneral_f, _g).
- * omega = 1 for initial conditions, 1 - 1/tau for post-collision rebuilds. */
+/* Grad populations h = h^eq (1 + omega * phi_h + w_pr * phi_h,q) in lattice
+ * (Ux, Uy) for the macroscopic state (rho, ux, uy, T) with velocity gradients
+ * du[a][b] = d_a u_b and temperature gradient dT[a] (Eqs. GradGeneral,
+ * GradGeneral_f, _g); phi_h,q is the heat-flux part of phi_h (all of phi_g).
+ * omega = 1, w_pr = 0 for initial conditions; omega = 1 - 1/tau and
+ * w_pr = 1/tau - 1/tau_Pr for post-collision rebuilds, which is the collision
+ * of App. E applied to the Grad population with q its Fourier heat flux. */
 int ora_grad_populations(const ora_config* cfg, int Ux, int Uy, double rho, double ux,
                          double uy, double T, const double du[2][2], const double dT[2],
-                         double omega, double f[ORA_Q], double g[ORA_Q]);
+                         double omega, double w_pr, double* f, double* g);
+
+/* Heat flux of one node's Q = 21 or 49 populations in lattice U (the flux of
+ * Eqs. Shakhov / prandtlPoly): q_a = 1/2 sum_i cbar_ia (|cbar_i|^2 f_i + g_i),
+ * cbar_i = xi_i + U - u, with u the node's velocity (absolute). */
+void ora_heat_flux(int Q, const double* f, const double* g, int Ux, int Uy, double ux,
+                   double uy, double q[2]);
 
 ora_state* ora_create(const ora_config* cfg);
 void ora_destroy(ora_state* s);

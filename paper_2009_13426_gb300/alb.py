@@ -28,6 +28,7 @@ ALB_ECUDA = -8
 ALB_ENOTFOUND = -9
 
 ALB_D2Q21 = 21
+ALB_D2Q49 = 49
 ALB_FP64_PLAIN = 0
 ALB_FP32_FORM = 1
 ALB_PERIODIC = 0
@@ -57,7 +58,8 @@ class alb_config(ctypes.Structure):
         ("sensor_eps", ctypes.c_double * 3), ("sensor_alpha", ctypes.c_double * 3),
         ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("newton_start", ctypes.c_int), ("shift_overlap", ctypes.c_double),
-        ("shift_rule", ctypes.c_int), ("moments", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("shift_rule", ctypes.c_int), ("moments", ctypes.c_int), ("prandtl", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
     ]
 
 
@@ -133,6 +135,10 @@ _SIGS = {
                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "alb_velocities": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "alb_stencil_velocities": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "alb_equilibrium13": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_double,
+                                                                  ctypes.c_int]
+                          + [ctypes.c_void_p] * 5),
     "alb_next_shifts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int]),
     "alb_populations": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int]),
@@ -346,6 +352,21 @@ def alb_velocities():
     return x, y
 
 
+def alb_stencil_velocities(stencil):
+    q = 49 if stencil == ALB_D2Q49 else Q
+    x = np.zeros(q, np.int32)
+    y = np.zeros(q, np.int32)
+    _check(lib().alb_stencil_velocities(int(stencil), x.ctypes.data, y.ctypes.data))
+    return x, y
+
+
+def alb_equilibrium13(rho, ubx, uby, T, n, tol, maxit, feq, lam, iters, status, stream=None):
+    """D2Q49 13-moment equilibria; torch CUDA tensors (float64; iters/status int32)."""
+    return _check(lib().alb_equilibrium13(_ptr(rho), _ptr(ubx), _ptr(uby), _ptr(T), int(n),
+                                          float(tol), int(maxit), _ptr(feq), _ptr(lam),
+                                          _ptr(iters), _ptr(status), _stream(stream)))
+
+
 def alb_batch_variants(precision):
     """[(block, min_blocks), ...] of the compiled batched-kernel variants."""
     n = ctypes.c_int()
@@ -449,12 +470,13 @@ class Flow:
         return ux.reshape(self.ny, self.nx), uy.reshape(self.ny, self.nx)
 
     def populations(self):
-        """(f, g), each (21, ny, nx) float64: the post-collision populations."""
-        n = self.nx * self.ny
-        f = np.empty(21 * n)
-        g = np.empty(21 * n)
+        """(f, g), each (Q, ny, nx) float64: the post-collision populations
+        (Q = 21, or 49 on D2Q49)."""
+        n, q = self.nx * self.ny, (49 if self.cfg.stencil == ALB_D2Q49 else 21)
+        f = np.empty(q * n)
+        g = np.empty(q * n)
         alb_populations(self.h, f, g)
-        return f.reshape(21, self.ny, self.nx), g.reshape(21, self.ny, self.nx)
+        return f.reshape(q, self.ny, self.nx), g.reshape(q, self.ny, self.nx)
 
     def primitives(self):
         n = self.nx * self.ny

@@ -84,6 +84,17 @@ int alb_velocities(int* xi_x, int* xi_y) {
   return ALB_OK;
 }
 
+int alb_stencil_velocities(int stencil, int* xi_x, int* xi_y) {
+  if (!xi_x || !xi_y) return fail(ALB_EINVAL, "alb_stencil_velocities: null pointer");
+  if (stencil == ALB_D2Q21) return alb_velocities(xi_x, xi_y);
+  if (stencil != ALB_D2Q49) return fail(ALB_EUNSUPPORTED, "unknown stencil %d", stencil);
+  for (int i = 0; i < 49; ++i) {
+    xi_x[i] = i % 7 - 3;
+    xi_y[i] = i / 7 - 3;
+  }
+  return ALB_OK;
+}
+
 int alb_config_default(alb_config* c) {
   if (!c) return fail(ALB_EINVAL, "alb_config_default: null pointer");
   memset(c, 0, sizeof(*c));
@@ -110,6 +121,7 @@ int alb_config_default(alb_config* c) {
   c->shift_overlap = 0.0;
   c->shift_rule = ALB_RULE_HISTORY;
   c->moments = 8;
+  c->prandtl = 1.0;
   c->stream = nullptr;
   return ALB_OK;
 }
@@ -122,7 +134,8 @@ static bool uses_previous_start(const alb_config* c) {
 
 static int check_config(const alb_config* c) {
   if (!c) return fail(ALB_EINVAL, "null config");
-  if (c->stencil != ALB_D2Q21) return fail(ALB_EUNSUPPORTED, "only ALB_D2Q21 is supported");
+  if (c->stencil != ALB_D2Q21 && c->stencil != ALB_D2Q49)
+    return fail(ALB_EUNSUPPORTED, "stencil must be ALB_D2Q21 or ALB_D2Q49");
   if (c->nx < 1 || c->ny < 1) return fail(ALB_EINVAL, "grid %d x %d is empty", c->nx, c->ny);
   if ((long long)c->nx * c->ny > (1LL << 31)) return fail(ALB_EINVAL, "grid too large");
   if (c->ny > 65535) return fail(ALB_EINVAL, "ny must be <= 65535");
@@ -147,8 +160,16 @@ static int check_config(const alb_config* c) {
     return fail(ALB_EINVAL, "shift_overlap must be in [0, 1]");
   if (c->shift_rule != ALB_RULE_HISTORY && c->shift_rule != ALB_RULE_NEIGHBOURS)
     return fail(ALB_EINVAL, "unknown shift_rule %d", c->shift_rule);
-  if (c->moments != 8 && c->moments != 4)
-    return fail(ALB_EINVAL, "moments must be 8 or 4");
+  if (c->stencil == ALB_D2Q21 && c->moments != 8 && c->moments != 4)
+    return fail(ALB_EINVAL, "moments must be 8 or 4 on D2Q21");
+  if (c->stencil == ALB_D2Q49) {
+    if (c->moments != 13) return fail(ALB_EINVAL, "moments must be 13 on D2Q49");
+    if (c->precision != ALB_FP64_PLAIN)
+      return fail(ALB_EUNSUPPORTED, "D2Q49 runs in ALB_FP64_PLAIN only");
+    if (c->newton_start == ALB_START_PREVIOUS)
+      return fail(ALB_EUNSUPPORTED, "D2Q49 solves start from the Maxwellian");
+  }
+  if (!(c->prandtl > 0.0 && c->prandtl < 1e300)) return fail(ALB_EINVAL, "prandtl must be > 0");
   return ALB_OK;
 }
 
@@ -185,6 +206,8 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.tol = cfg->newton_tol;
   p.cv = 1.0 / (cfg->gamma - 1.0);
   p.cp = cfg->gamma * p.cv;
+  p.shakhov = cfg->prandtl != 1.0 ? 1 : 0;
+  p.prandtl = cfg->prandtl;
   for (int j = 0; j < 3; ++j) {
     p.seps[j] = cfg->sensor_eps[j];
     p.salpha[j] = cfg->sensor_alpha[j];
@@ -203,6 +226,8 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
     p.whi[j] = ((double)(j - 2) - cfg->n0) + cfg->shift_overlap;
   }
   d.precision = cfg->precision;
+  d.q = cfg->stencil == ALB_D2Q49 ? 49 : Q;
+  d.nplanes = 2 * d.q;
   d.n = (size_t)cfg->nx * cfg->ny;
   d.ps = (d.n + 63) / 64 * 64;
   d.cur = 0;
@@ -229,7 +254,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
     }                                                                  \
   } while (0)
   for (int b = 0; b < 2; ++b) {
-    ALLOC(d.pop[b], NPLANES * d.ps * es);
+    ALLOC(d.pop[b], (size_t)d.nplanes * d.ps * es);
     ALLOC(d.mom[b], 4 * d.ps * es);
     ALLOC(d.lat[b], d.ps);
     ALLOC(d.nxt[b], d.ps);
@@ -403,7 +428,7 @@ int alb_populations(alb_handle* h, double* f, double* g, int where) {
   if (!h || !f || !g) return fail(ALB_EINVAL, "alb_populations: null pointer");
   if (!h->initialised) return fail(ALB_EINVAL, "alb_populations: call alb_init first");
   double* outs[2] = {f, g};
-  return export_planes(h, 0, outs, 2, Q, where, "alb_populations");
+  return export_planes(h, 0, outs, 2, h->dev.q, where, "alb_populations");
 }
 
 int alb_primitives(alb_handle* h, double* rho, double* ux, double* uy, double* T, int where) {
@@ -418,7 +443,7 @@ int alb_primitives(alb_handle* h, double* rho, double* ux, double* uy, double* T
 struct CheckpointHeader {
   char magic[8];          // "ALBCKPT1"
   int32_t nx, ny, precision, warm;
-  int32_t u_max, bc_x, bc_y, reserved;
+  int32_t u_max, bc_x, bc_y, q;  // q: velocities per node (0 read as 21)
   uint64_t ps, steps;
 };
 
@@ -432,7 +457,7 @@ static int checkpoint_pieces(alb_handle* h, Piece* out) {
   const size_t es = d.precision == ALB_FP64_PLAIN ? sizeof(double) : sizeof(float);
   const int b = d.cur;
   int k = 0;
-  out[k++] = {d.pop[b], NPLANES * d.ps * es};
+  out[k++] = {d.pop[b], (size_t)d.nplanes * d.ps * es};
   out[k++] = {d.mom[b], 4 * d.ps * es};
   out[k++] = {d.lat[b], d.ps};
   out[k++] = {d.nxt[b], d.ps};
@@ -464,6 +489,7 @@ int alb_checkpoint_save(alb_handle* h, void* buf) {
   hd.u_max = h->cfg.u_max;
   hd.bc_x = h->cfg.bc_x;
   hd.bc_y = h->cfg.bc_y;
+  hd.q = h->dev.q;
   hd.ps = h->dev.ps;
   hd.steps = h->steps;
   unsigned char* p = (unsigned char*)buf;
@@ -488,7 +514,7 @@ int alb_checkpoint_load(alb_handle* h, const void* buf) {
     return fail(ALB_EINVAL, "alb_checkpoint_load: not a checkpoint of this library");
   if (hd.nx != h->cfg.nx || hd.ny != h->cfg.ny || hd.precision != h->dev.precision ||
       hd.warm != h->dev.prm.warm || hd.u_max != h->cfg.u_max || hd.bc_x != h->cfg.bc_x ||
-      hd.bc_y != h->cfg.bc_y || hd.ps != h->dev.ps)
+      hd.bc_y != h->cfg.bc_y || hd.ps != h->dev.ps || (hd.q ? hd.q : Q) != h->dev.q)
     return fail(ALB_EINVAL, "alb_checkpoint_load: checkpoint of another configuration");
   ALB_CUDA(cudaStreamSynchronize(h->stream), "alb_checkpoint_load: synchronise");
   const unsigned char* p = (const unsigned char*)buf + sizeof(hd);
@@ -564,6 +590,17 @@ int alb_equilibrium(const double* rho, const double* ubx, const double* uby, con
   return ALB_OK;
 }
 
+int alb_equilibrium13(const double* rho, const double* ubx, const double* uby, const double* T,
+                      int n, double tol, int maxit, double* feq, double* lambda, int* iters,
+                      int* status, void* stream) {
+  if (n < 0 || (n > 0 && (!rho || !ubx || !uby || !T || !feq || !lambda || !iters || !status)))
+    return fail(ALB_EINVAL, "alb_equilibrium13: bad arguments");
+  if (!(tol > 0.0) || maxit < 1) return fail(ALB_EINVAL, "alb_equilibrium13: bad tolerance");
+  ALB_CUDA(launch_equilibrium13(rho, ubx, uby, T, n, tol, maxit, feq, lambda, iters, status,
+                                (cudaStream_t)stream), "alb_equilibrium13");
+  return ALB_OK;
+}
+
 int alb_exp_neg(const double* s, int n, double* out, void* stream) {
   if (n < 0 || (n > 0 && (!s || !out))) return fail(ALB_EINVAL, "alb_exp_neg: bad arguments");
   ALB_CUDA(launch_exp_neg(s, n, out, (cudaStream_t)stream), "alb_exp_neg");
@@ -590,7 +627,8 @@ int config_check(const alb_config* c) { return check_config(c); }
 size_t flow_device_bytes(const alb_config* c) {
   const size_t n = (size_t)c->nx * c->ny, ps = (n + 63) / 64 * 64;
   const size_t es = c->precision == ALB_FP64_PLAIN ? sizeof(double) : sizeof(float);
-  size_t b = 2 * (NPLANES * ps * es + 4 * ps * es + 2 * ps);
+  const size_t np = c->stencil == ALB_D2Q49 ? 98 : NPLANES;
+  size_t b = 2 * (np * ps * es + 4 * ps * es + 2 * ps);
   if (uses_previous_start(c)) b += 2 * NM * ps * es;
   b += CTR_COUNT * sizeof(unsigned long long) + 4 * n * sizeof(double) +
        (size_t)(totals_blocks((long long)n) + 1) * 4 * sizeof(double) + 4 * sizeof(double);

@@ -424,6 +424,10 @@ int alb_batch_create(const alb_config* cfgs, int nflows, void* stream, alb_batch
   for (int i = 0; i < nflows; ++i) {
     alb_config c = cfgs[i];
     c.stream = b->stream;
+    if (c.stencil != ALB_D2Q21) {
+      alb_batch_destroy(b);
+      return set_error(ALB_EUNSUPPORTED, "alb_batch_create: flow %d: batches run D2Q21 only", i);
+    }
     alb_handle* h = nullptr;
     const int rc = alb_create(&c, &h);
     if (rc != ALB_OK) {

@@ -52,7 +52,9 @@ struct Params {
   int warm;          // 1: solves start from the previous step's multipliers
   int rule;          // where ranges overlap: 0 history, 1 neighbourhood
   int moments;       // constraint set: 8, or 4 (reduced model)
+  int shakhov;       // 1: Pr != 1, heat-flux term of App. E in the collision
   double nu, gamma, n0, tol;
+  double prandtl;    // Pr: tau_Pr = 1/2 + (nu/Pr)/T, kappa = rho Cp nu / Pr
   double overlap;    // widening of the current shift's range (0: Eq. criterion)
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
   double seps[3], salpha[3];
@@ -198,14 +200,15 @@ __device__ __forceinline__ double exp_family_one(const double lam[NM], int cx, i
   return exp(-s);
 }
 
-// Grad's correction factors (Eqs. GradGeneral_f, GradGeneral_g) for one
-// velocity: cbar = c_i - u, sigma traceless viscous stress with mu = rho nu,
-// q = -kappa grad T with kappa = rho Cp nu (Pr = 1). du[a][b] = d_a u_b.
+// Grad's factors (Eqs. GradGeneral_f, GradGeneral_g) for cbar = c_i - u:
+// phi_f = phi_s + phi_q with phi_s the traceless viscous stress part (mu =
+// rho nu) and phi_q the Fourier heat-flux part (kappa = rho Cp nu / Pr), and
+// phi_g. phi_q has the shape of the heat-flux term of App. E.
 __device__ __forceinline__ void grad_phi(const Params& pr, double rho, double T, double cbx,
                                          double cby, const double du[2][2], const double dT[2],
-                                         double* phi_f, double* phi_g) {
+                                         double* phi_f, double* phi_g, double* phi_q) {
   const double mu = rho * pr.nu;
-  const double kappa = rho * pr.cp * pr.nu;
+  const double kappa = rho * pr.cp * pr.nu / pr.prandtl;
   const double div = du[0][0] + du[1][1];
   const double sxx = -mu * (2.0 * du[0][0] - div);
   const double syy = -mu * (2.0 * du[1][1] - div);
@@ -215,8 +218,11 @@ __device__ __forceinline__ void grad_phi(const Params& pr, double rho, double T,
   const double c2 = cbx * cbx + cby * cby;
   const double qc = qx * cbx + qy * cby;
   const double iT = 1.0 / T;
-  *phi_f = (sxx * cbx * cbx + 2.0 * sxy * cbx * cby + syy * cby * cby) * (0.5 * iT * iT / rho) +
-           qc * (iT * iT / (rho * pr.cp)) * (0.5 * c2 * iT - pr.cp);
+  const double ps = (sxx * cbx * cbx + 2.0 * sxy * cbx * cby + syy * cby * cby) *
+                    (0.5 * iT * iT / rho);
+  const double pq = qc * (iT * iT / (rho * pr.cp)) * (0.5 * c2 * iT - pr.cp);
+  *phi_f = ps + pq;
+  *phi_q = pq;
   *phi_g = 2.0 * qc / (rho * pr.cp);
 }
 

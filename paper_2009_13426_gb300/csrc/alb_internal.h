@@ -28,9 +28,11 @@ enum Counter {
 struct FlowDev {
   Params prm;
   int precision;     // 0 FP64 plain, 1 FP32 form
+  int q;             // velocities: 21 (D2Q21) or 49 (D2Q49 reference solver)
+  int nplanes;       // population planes, 2 q
   size_t n;          // nx * ny
   size_t ps;         // plane stride in elements (n rounded up to 64)
-  void* pop[2];      // 42 planes of double or float
+  void* pop[2];      // nplanes planes of double or float
   void* mom[2];      // 4 planes (rho, ux, uy, T) of double or float
   uint8_t* lat[2];   // lattice code of the stored populations
   uint8_t* nxt[2];   // lattice code selected for the next pull
@@ -95,6 +97,13 @@ cudaError_t launch_equilibrium(const double* rho, const double* ubx, const doubl
                                double* feq, double* lambda, int* iters, int* status,
                                cudaStream_t s);
 cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s);
+// D2Q49 reference solver (alb_q49.cu), FP64 only.
+cudaError_t launch_init_q49(FlowDev& f, const double* rho, const double* rhoux,
+                            const double* rhouy, const double* rhoE, cudaStream_t s);
+cudaError_t launch_step_q49(FlowDev& f, cudaStream_t s);
+cudaError_t launch_equilibrium13(const double* rho, const double* ubx, const double* uby,
+                                 const double* T, int n, double tol, int maxit, double* feq,
+                                 double* lambda, int* iters, int* status, cudaStream_t s);
 cudaError_t launch_select(const double* rho, const double* rhou, int n, double n0, int umax,
                           signed char* out, cudaStream_t s);
 

@@ -104,10 +104,10 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
     for (int i = 0; i < Q; ++i) {
       const double cbx = (double)(XI_X(i) + U0x) - ux;
       const double cby = (double)(XI_Y(i) + U0y) - uy;
-      double phf = 0.0, phg = 0.0;
+      double phf = 0.0, phg = 0.0, phq = 0.0;
       double feq = 0.0;
       if (ns == NEWTON_OK) {
-        grad_phi(pr, r, T, cbx, cby, du, dT, &phf, &phg);
+        grad_phi(pr, r, T, cbx, cby, du, dT, &phf, &phg, &phq);
         feq = r * cl.eq[i * BLOCK];
       }
       cl.pop[i * BLOCK] = (P)(feq * (1.0 + phf));
@@ -246,6 +246,7 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
 
 cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, const double* rhouy,
                         const double* rhoE, cudaStream_t s) {
+  if (f.q == 49) return launch_init_q49(f, rho, rhoux, rhouy, rhoE, s);
   const int out = f.cur;
   cudaError_t e;
   if (f.precision == 0) {
@@ -263,6 +264,7 @@ cudaError_t launch_init(FlowDev& f, const double* rho, const double* rhoux, cons
 }
 
 cudaError_t launch_step(FlowDev& f, cudaStream_t s) {
+  if (f.q == 49) return launch_step_q49(f, s);
   const int in = f.cur, out = f.cur ^ 1;
   cudaError_t e;
   if (f.precision == 0) {

@@ -435,6 +435,8 @@ int alb_submit(alb_server* s, const alb_request* r, uint64_t* id) {
   if (!s || !r || !id) return set_error(ALB_EINVAL, "alb_submit: null pointer");
   int rc = config_check(&r->cfg);
   if (rc != ALB_OK) return rc;
+  if (r->cfg.stencil != ALB_D2Q21)
+    return set_error(ALB_EUNSUPPORTED, "alb_submit: the server runs D2Q21 flows only");
   if (r->nsteps < 0) return set_error(ALB_EINVAL, "alb_submit: nsteps < 0");
   const bool copy = r->rho || r->rhoux || r->rhouy || r->rhoE;
   if (copy && !(r->rho && r->rhoux && r->rhouy && r->rhoE))

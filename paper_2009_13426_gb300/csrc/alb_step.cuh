@@ -119,9 +119,10 @@ __device__ __forceinline__ void load_warm(const L* lam, size_t ps, size_t k, int
 // population of velocity i = (cx, cy) in the receiver's lattice (Upx, Upy),
 // built from the sender's moments at (sx, sy) (possibly a ghost), their
 // central differences and the sender's relaxation time:
-// h* = h^eq (1 + (1 - 1/tau) phi_h). Uses the thread's equilibrium column as
-// scratch. Returns 1 if the root finder failed and the Maxwellian-guess
-// fallback was used.
+// h* = h^eq (1 + (1 - 1/tau) phi_h), plus (1/tau - 1/tau_Pr) h^eq phi_h,q for
+// Pr != 1 (the collision of App. E applied to the Grad population). Uses the
+// thread's equilibrium column as scratch. Returns 1 if the root finder failed
+// and the Maxwellian-guess fallback was used.
 template <typename P, int B>
 __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
                                          int i, int cx, int cy, int Upx, int Upy, int sx, int sy,
@@ -177,11 +178,64 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   const double feq = rho * eq[i * B];
   const double cbx = (double)(cx + Upx) - ux;
   const double cby = (double)(cy + Upy) - uy;
-  double phf, phg;
-  grad_phi(pr, rho, T, cbx, cby, du, dT, &phf, &phg);
-  *fi = feq * (1.0 + omega * phf);
-  *gi = gfac * feq * (1.0 + omega * phg);
+  double phf, phg, phq;
+  grad_phi(pr, rho, T, cbx, cby, du, dT, &phf, &phg, &phq);
+  if (pr.shakhov) {
+    const double w = 1.0 / tau - 1.0 / (0.5 + (pr.nu / pr.prandtl) / T);
+    *fi = feq * (1.0 + omega * phf + w * phq);
+    *gi = gfac * feq * (1.0 + omega * phg + w * phg);
+  } else {
+    *fi = feq * (1.0 + omega * phf);
+    *gi = gfac * feq * (1.0 + omega * phg);
+  }
   return 0;
+}
+
+// Store of a collided node for Pr != 1: BGK plus the heat-flux term of App. E
+// (Eqs. Shakhov, prandtlPoly),
+//   f* += (1/tau - 1/tau_Pr) q.cbar / (rho Cp T^2) (|cbar|^2 / (2T) - Cp) f^eq,
+//   g* += (1/tau - 1/tau_Pr) 2 q.cbar / (rho Cp) g^eq,
+// with q_a = 1/2 sum_i cbar_ia (|cbar_i|^2 f_i + g_i) of the pre-collision
+// populations st, cbar_i = xi_i - (u - U) (lattice frame, U of lattice
+// `code`), tau_Pr = 1/2 + (nu/Pr)/T, both relaxation times scaled by the
+// sensor factor tau / (1/2 + nu/T).
+template <typename P, int B>
+__device__ __forceinline__ void store_shakhov(const Params& pr, const P* st, const double* eq,
+                                              double rho, double ux, double uy, double T,
+                                              int code, P tau, size_t k, size_t ps,
+                                              P* __restrict__ pop_out) {
+  const P Tp = (P)T, rp = (P)rho;
+  const P bx = (P)(ux - (double)lat_ux(code)), by = (P)(uy - (double)lat_uy(code));
+  const P cp = (P)pr.cp;
+  const P gp = ((P)2 * (P)pr.cv - (P)2) * Tp;
+  const P tau_pr = ((P)0.5 + (P)(pr.nu / pr.prandtl) / Tp) * (tau / ((P)0.5 + (P)pr.nu / Tp));
+  const P om = (P)1 / tau;
+  const P w = om - (P)1 / tau_pr;
+  P qx = 0, qy = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const P cx = (P)XI_X(i) - bx, cy = (P)XI_Y(i) - by;
+    const P e = (cx * cx + cy * cy) * st[i * B] + st[(Q + i) * B];
+    qx += cx * e;
+    qy += cy * e;
+  }
+  qx *= (P)0.5;
+  qy *= (P)0.5;
+  const P af = w / (rp * cp * Tp * Tp);
+  const P ag = w * (P)2 / (rp * cp);
+  const P h = (P)0.5 / Tp;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const P fe = (P)eq[i * B] * rp;
+    const P ge = gp * fe;
+    const P f = st[i * B];
+    const P g = st[(Q + i) * B];
+    const P cx = (P)XI_X(i) - bx, cy = (P)XI_Y(i) - by;
+    const P c2 = cx * cx + cy * cy;
+    const P qc = qx * cx + qy * cy;
+    pop_out[i * ps + k] = fma(om, fe - f, f) + af * qc * (c2 * h - cp) * fe;
+    pop_out[(Q + i) * ps + k] = fma(om, ge - g, g) + ag * qc * ge;
+  }
 }
 
 // Moments, next shift, equilibrium and BGK of one node whose 42 pre-collision
@@ -256,15 +310,19 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
       eps /= (P)Q;
       tau *= sensor_alpha<P>(pr, eps);
     }
-    const P om = (P)1 / tau;
+    if (pr.shakhov) {
+      store_shakhov<P, B>(pr, st, cl.eq, rho, ux, uy, T, code, tau, k, ps, pop_out);
+    } else {
+      const P om = (P)1 / tau;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const P fe = (P)cl.eq[i * B] * rp;
-      const P ge = gp * fe;
-      const P f = st[i * B];
-      const P g = st[(Q + i) * B];
-      pop_out[i * ps + k] = fma(om, fe - f, f);
-      pop_out[(Q + i) * ps + k] = fma(om, ge - g, g);
+      for (int i = 0; i < Q; ++i) {
+        const P fe = (P)cl.eq[i * B] * rp;
+        const P ge = gp * fe;
+        const P f = st[i * B];
+        const P g = st[(Q + i) * B];
+        pop_out[i * ps + k] = fma(om, fe - f, f);
+        pop_out[(Q + i) * ps + k] = fma(om, ge - g, g);
+      }
     }
   } else {
     *n_fail += 1;

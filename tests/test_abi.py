@@ -51,6 +51,7 @@ def test_binding_covers_the_header(lib):
 def test_host_side_calls_without_gpu(lib):
     cfg = lib.alb_config_default()
     assert cfg.nx == 64 and cfg.stencil == 21 and cfg.newton_tol == 1e-12
+    assert cfg.moments == 8 and cfg.prandtl == 1.0 and cfg.stream is None
     x, y = lib.alb_velocities()
     import oracle as O
     ox, oy = O.velocities()

@@ -22,6 +22,8 @@ def lib():
     ("precision", 5), ("bc_x", 3), ("bc_y", -1),
     ("newton_tol", 0.0), ("newton_maxit", 0), ("newton_start", 7),
     ("shift_overlap", -0.1), ("shift_overlap", 1.5), ("shift_rule", 2), ("moments", 6),
+    ("prandtl", 0.0), ("prandtl", -0.7), ("prandtl", float("nan")), ("prandtl", float("inf")),
+    ("moments", 13),                                  # 13 moments belong to D2Q49
 ])
 def test_configuration_out_of_range_is_refused(lib, field, value):
     cfg = lib.alb_config_default(**{field: value})
@@ -73,3 +75,16 @@ def test_batch_and_server_arguments_are_checked(lib):
         lib.alb_batch_variants(9)
     assert ei.value.code == lib.ALB_EINVAL
     assert lib.alb_batch_variants(lib.ALB_FP32_FORM)[0] == (128, 4)
+
+
+@pytest.mark.parametrize("fields,code", [
+    (dict(stencil=49), "EINVAL"),                     # D2Q49 needs moments = 13
+    (dict(stencil=49, moments=13, precision=1), "EUNSUPPORTED"),
+    (dict(stencil=49, moments=13, newton_start=2), "EUNSUPPORTED"),
+    (dict(stencil=37), "EUNSUPPORTED"),
+])
+def test_d2q49_configuration_limits(lib, fields, code):
+    cfg = lib.alb_config_default(**fields)
+    with pytest.raises(lib.AlbError) as ei:
+        lib.alb_create(cfg)
+    assert ei.value.code == getattr(lib, "ALB_" + code)

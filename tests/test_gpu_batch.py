@@ -161,3 +161,28 @@ def test_batch_errors(alb):
             alb.alb_batch_flow(b.b, 5)
     finally:
         b.close()
+
+
+def test_prandtl_flows_in_a_batch(alb):
+    """Flows with Pr != 1 (App. E) in a batch, next to BGK flows: bit-identical
+    to each flow run alone."""
+    specs = [(SPECS[0], 0.71), (SPECS[1], 1.0), (SPECS[4], 2.0), (SPECS[5], 0.5)]
+    cfgs = [dict(cfg_of(alb, sp), prandtl=pr) for sp, pr in specs]
+    ref = []
+    for (sp, _), c in zip(specs, cfgs):
+        fl = alb.Flow(**c)
+        fl.init(*sp.fields())
+        fl.step(STEPS)
+        fl.sync()
+        ref.append(state(fl))
+        fl.close()
+    b = alb.Batch(cfgs)
+    try:
+        for (sp, _), fl in zip(specs, b.flows):
+            fl.init(*sp.fields())
+        b.step(STEPS)
+        b.sync()
+        for k, fl in enumerate(b.flows):
+            assert_same(state(fl), ref[k], "flow %d" % k)
+    finally:
+        b.close()

@@ -232,6 +232,54 @@ def test_vortex_reduced_model_matches_oracle(alb, precision):
     assert max(err.values()) <= tol, err
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vortex_prandtl_matches_oracle(alb, precision):
+    """Pr = 0.71 (App. E): the heat-flux term in every collision, kappa =
+    rho Cp nu / Pr in the initial state and in Grad rebuilds, which carry the
+    term too. 64^2 vortex at Mach 1.2, nu = 0.02, 60 steps: FP64 plain against
+    the free-running oracle (1e-11, shifts and rebuild counts equal), FP32
+    form with replayed decisions (1e-5). The flow differs from the Pr = 1 one
+    by about 2 %."""
+    fields = flows.isentropic_vortex()
+    kw = dict(umax=2, nu=0.02, prandtl=0.71)
+    if precision == 0:
+        s, st = run_oracle(64, 64, fields, 60, **kw)
+        assert st == O.OK
+        fl = run_gpu(alb, 64, 64, fields, 60, alb.ALB_FP64_PLAIN, **kw)
+        sx, sy = fl.shifts()
+        rx, ry = s.shifts()
+        assert (sx == rx).all() and (sy == ry).all()
+        assert fl.stats()["reconstructions"] == s.stats()["reconstructions"]
+        tol = FP64_TOL
+    else:
+        fl, s, _ = run_replay(alb, 64, 64, fields, 60, alb.ALB_FP32_FORM, **kw)
+        tol = FP32_TOL
+    err = rel_errors(fl.moments(), s.moments())
+    assert max(err.values()) <= tol, err
+    bgk = run_gpu(alb, 64, 64, fields, 60, precision, umax=2, nu=0.02)
+    assert max(rel_errors(bgk.moments(), s.moments()).values()) > 1e-3
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_sod_prandtl_with_sensor_matches_oracle(alb, precision, tol):
+    """Pr = 0.5 with the kinetic sensor (both relaxation times scaled by its
+    factor) on a 512 x 4 Sod tube, zero-gradient x ends, 150 steps."""
+    nx, ny, steps = 512, 4, 150
+    fields = flows.riemann_1d(nx, ny)
+    kw = dict(umax=2, nu=1e-3, bc_x=O.ZERO_GRADIENT, sensor=True, prandtl=0.5)
+    if precision == 0:
+        s, st = run_oracle(nx, ny, fields, steps, **kw)
+        assert st == O.OK
+        fl = run_gpu(alb, nx, ny, fields, steps, precision, **kw)
+        sx, sy = fl.shifts()
+        rx, ry = s.shifts()
+        assert (sx == rx).all() and (sy == ry).all()
+    else:
+        fl, s, _ = run_replay(alb, nx, ny, fields, steps, precision, **kw)
+    err = rel_errors(fl.moments(), s.moments())
+    assert max(err.values()) <= tol, err
+
+
 def test_neighbourhood_rule_at_zero_gradient_ends(alb):
     """The neighbourhood rule reads ghost neighbours through the boundary
     rule: a ragged grid with zero-gradient ends in x and y, FP64 plain."""
