@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-overlap", action="store_true")
+    ap.add_argument("--no-d2q49", action="store_true",
+                    help="skip the D2Q49 reference-solver line")
+    ap.add_argument("--d2q49-side", type=int, default=1024)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-flows", type=int, default=256,
@@ -536,6 +539,35 @@ def run_ours(args, world, rank, local):
                                                          / (N * args.steps), 4)}
             flo.close()
 
+    # the paper's reference solver (App. C.1): D2Q49, 13 moments, FP64, on the
+    # same shear-layer recipe at a smaller side
+    q49 = None
+    if not args.no_d2q49:
+        n49 = args.d2q49_side
+        f49 = fields if n49 == n else flows.shear_layer(n49)
+        fl = alb.Flow(n49, n49, stencil=alb.ALB_D2Q49, moments=13, u_max=2, nu=NU,
+                      precision=alb.ALB_FP64_PLAIN, stream=stream)
+        fl.init(*f49)
+        k49 = max(2, args.steps // 4)
+        ms49, d49 = timed(fl, k49, min(args.warmup, 2))
+        N49 = n49 * n49
+        q49 = {"workload": "shear layer %dx%d (the headline's recipe), D2Q49, 13 moments, "
+                           "FP64" % (n49, n49),
+               "value": round(N49 * k49 / (ms49 * 1e-3) / 1e6, 2), "unit": UNIT,
+               "steps": k49, "ms_per_step": round(ms49 / k49, 3),
+               "kernel": "q49::step_kernel",
+               "per_node": {k: round(d49[k] / (N49 * k49), 4)
+                            for k in ("newton_iterations", "newton_calls", "reconstructions")},
+               "failures": {"node": d49["newton_failures"],
+                            "rebuild": d49["reconstruction_failures"]}}
+        slots49 = costmodel.q49_slots(d49, N49 * k49)
+        if slots49:
+            t49 = 2.0 * slots49 / (ms49 * 1e-3) / 1e12
+            q49["roofline"] = {"bound": "alu", "achieved": round(t49, 4),
+                               "peak": round(costmodel.FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                               "frac": round(t49 / costmodel.FP64_PEAK_TFLOPS, 4)}
+        fl.close()
+
     e2e = None
     if not args.no_e2e:
         pinned = [torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).pin_memory() for a in fields]
@@ -597,6 +629,8 @@ def run_ours(args, world, rank, local):
     line.update(extra)
     if ovl:
         line["overlapping_ranges"] = ovl
+    if q49:
+        line["reference_solver_d2q49"] = q49
     if batched:
         line["batched"] = batched
     if serve:

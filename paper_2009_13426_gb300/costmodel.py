@@ -164,3 +164,20 @@ def describe():
 
 if __name__ == "__main__":
     print(describe())
+
+
+# ---------------------------------------------------------------- D2Q49
+
+# FP64-pipe slots of the D2Q49 step per unit of work, measured with ncu on the
+# 256^2 shear layer (profiles/q49_step_kernel.md); None until measured.
+Q49_PER_ITER = None
+Q49_PER_CALL = None
+Q49_PER_NODE = None
+
+
+def q49_slots(delta, node_updates):
+    """FP64 slots of D2Q49 launches from their counters, or None."""
+    if Q49_PER_ITER is None:
+        return None
+    return (Q49_PER_ITER * delta["newton_iterations"] + Q49_PER_CALL * delta["newton_calls"]
+            + Q49_PER_NODE * node_updates)

@@ -7,7 +7,10 @@
 // Velocity i = (x, y) has index i = (x + 3) + 7 (y + 3). One thread per node;
 // a block is a row segment of B nodes. Each thread owns two columns of the
 // block's dynamic shared memory (stride B): its 98 pulled populations and the
-// 49 equilibrium values per unit density of its latest solve.
+// 49 equilibrium values per unit density of its latest solve. Missing pulls
+// go to a block-wide queue and are rebuilt round-robin by all threads of the
+// block, so that a warp does not wait for its lanes' rebuilds one by one.
+// Exponentials use the table-driven FP64 exp of the D2Q21 kernels.
 //
 // Newton on the 13 multipliers follows the 8-moment solver's iteration
 // (Maxwellian start with lambda_0 from the normalisation, exact Jacobian,
@@ -16,6 +19,7 @@
 // is a tensor product, so they come from per-row sums S_a(y) = sum_x p x^a
 // (756 multiply-adds instead of 49 x 91).
 #include "alb_internal.h"
+#include "alb_mixed.cuh"
 
 namespace alb {
 namespace q49 {
@@ -94,11 +98,11 @@ __device__ __forceinline__ double lam_dot(const double l[M], int i) {
 }
 
 // p_i = exp(-(1 + lambda . P_i)) into eq (stride B); returns sum_i p_i.
-__device__ __forceinline__ double eval_p(const double l[M], double* eq) {
+__device__ __forceinline__ double eval_p(const double l[M], double* eq, const double* tab) {
   double z = 0.0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const double p = exp(-(1.0 + lam_dot(l, i)));
+    const double p = exp_neg(1.0 + lam_dot(l, i), tab);
     eq[i * B] = p;
     z += p;
   }
@@ -135,7 +139,7 @@ enum { OK = NEWTON_OK, MAXIT = NEWTON_MAXIT, SINGULAR = NEWTON_SINGULAR };
 // Newton on the 13 multipliers for (ubx, uby, T) in the lattice frame; the
 // equilibrium per unit density is left in eq (stride B).
 __device__ __noinline__ int newton13(double ubx, double uby, double T, double tol, int maxit,
-                                     double* eq, double lam[M], int* iters) {
+                                     double* eq, const double* tab, double lam[M], int* iters) {
   *iters = 0;
   if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
   double m[M];
@@ -147,8 +151,16 @@ __device__ __noinline__ int newton13(double ubx, double uby, double T, double to
   l[2] = -uby / T;
   l[3] = 0.5 / T;
   l[5] = 0.5 / T;
-  l[0] = log(eval_p(l, eq));
-  double F = eval_p(l, eq);
+  // lambda_0 = ln Z normalises the start; p = exp(-(1 + rest)) / Z
+  const double Z = eval_p(l, eq, tab);
+  l[0] = log(Z);
+  const double iz = 1.0 / Z;
+  double F = 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    eq[i * B] *= iz;
+    F += eq[i * B];
+  }
 #pragma unroll
   for (int k = 0; k < M; ++k) F += l[k] * m[k];
   int status = MAXIT, it = 0;
@@ -182,6 +194,7 @@ __device__ __noinline__ int newton13(double ubx, double uby, double T, double to
             s += Mab[term(r, t).a + term(c, u).a][term(r, t).b + term(c, u).b];
         H[r * (r + 1) / 2 + c] = s;
       }
+    // Cholesky H = L L^T in place; the diagonal keeps 1 / L_jj
     bool spd = true;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -189,14 +202,14 @@ __device__ __noinline__ int newton13(double ubx, double uby, double T, double to
 #pragma unroll
       for (int k = 0; k < j; ++k) d -= H[j * (j + 1) / 2 + k] * H[j * (j + 1) / 2 + k];
       if (!(d > 0.0) || !isfinite(d)) spd = false;
-      const double ljj = sqrt(d);
-      H[j * (j + 1) / 2 + j] = ljj;
+      const double inv = 1.0 / sqrt(d);
+      H[j * (j + 1) / 2 + j] = inv;
 #pragma unroll
       for (int i = j + 1; i < M; ++i) {
         double t = H[i * (i + 1) / 2 + j];
 #pragma unroll
         for (int k = 0; k < j; ++k) t -= H[i * (i + 1) / 2 + k] * H[j * (j + 1) / 2 + k];
-        H[i * (i + 1) / 2 + j] = t / ljj;
+        H[i * (i + 1) / 2 + j] = t * inv;
       }
     }
     if (!spd) { status = SINGULAR; break; }
@@ -206,14 +219,14 @@ __device__ __noinline__ int newton13(double ubx, double uby, double T, double to
       double t = G[i];
 #pragma unroll
       for (int k = 0; k < i; ++k) t -= H[i * (i + 1) / 2 + k] * d[k];
-      d[i] = t / H[i * (i + 1) / 2 + i];
+      d[i] = t * H[i * (i + 1) / 2 + i];
     }
 #pragma unroll
     for (int i = M - 1; i >= 0; --i) {
       double t = d[i];
 #pragma unroll
       for (int k = i + 1; k < M; ++k) t -= H[k * (k + 1) / 2 + i] * d[k];
-      d[i] = t / H[i * (i + 1) / 2 + i];
+      d[i] = t * H[i * (i + 1) / 2 + i];
     }
     double gd = 0.0;
 #pragma unroll
@@ -224,7 +237,7 @@ __device__ __noinline__ int newton13(double ubx, double uby, double T, double to
     for (int ls = 0; ls < 40; ++ls) {
 #pragma unroll
       for (int k = 0; k < M; ++k) lc[k] = l[k] + t * d[k];
-      Fc = eval_p(lc, eq);
+      Fc = eval_p(lc, eq, tab);
 #pragma unroll
       for (int k = 0; k < M; ++k) Fc += lc[k] * m[k];
       if (isfinite(Fc) && Fc <= F - 1e-4 * t * gd + 1e-15 * fabs(F)) {
@@ -255,7 +268,7 @@ struct Count {
 // the Maxwellian exponential normalised over the lattice if the solve fails.
 __device__ __noinline__ int rebuild(const Params pr, const double* __restrict__ mom, size_t ps,
                                     int i, int Upx, int Upy, int sx, int sy, double* fi,
-                                    double* gi, double* eq, Count* cnt) {
+                                    double* gi, double* eq, const double* tab, Count* cnt) {
   bool gh = false;
   const int rx = resolve(sx, pr.nx, pr.bcx, &gh), ry = resolve(sy, pr.ny, pr.bcy, &gh);
   const int xp = resolve(sx + 1, pr.nx, pr.bcx, &gh), xm = resolve(sx - 1, pr.nx, pr.bcx, &gh);
@@ -277,7 +290,7 @@ __device__ __noinline__ int rebuild(const Params pr, const double* __restrict__ 
   const double ubx = ux - Upx, uby = uy - Upy;
   double lam[M];
   int it = 0;
-  const int st = rho > 0.0 ? newton13(ubx, uby, T, pr.tol, pr.maxit, eq, lam, &it)
+  const int st = rho > 0.0 ? newton13(ubx, uby, T, pr.tol, pr.maxit, eq, tab, lam, &it)
                            : NEWTON_UNREALIZABLE;
   cnt->iters += it;
   cnt->calls += 1;
@@ -331,7 +344,8 @@ __device__ __forceinline__ void neighbours(const Params& pr, const uint8_t* cur,
 __device__ __forceinline__ void collide(const Params& pr, const double* col, double* eq, int code,
                                         size_t k, size_t ps, double* __restrict__ pop_out,
                                         double* __restrict__ mom_out, uint8_t* lat_out,
-                                        uint8_t* nxt_out, const uint8_t* nb, Count* cnt) {
+                                        uint8_t* nxt_out, const uint8_t* nb, const double* tab,
+                                        Count* cnt) {
   const int Ux = lat_ux(code), Uy = lat_uy(code);
   double rho = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
 #pragma unroll
@@ -351,7 +365,7 @@ __device__ __forceinline__ void collide(const Params& pr, const double* col, dou
                           : lat_code(select_shift_kept(ux, Ux, pr), select_shift_kept(uy, Uy, pr));
   double lam[M];
   int it = 0;
-  const int ns = rho > 0.0 ? newton13(ubx, uby, T, pr.tol, pr.maxit, eq, lam, &it)
+  const int ns = rho > 0.0 ? newton13(ubx, uby, T, pr.tol, pr.maxit, eq, tab, lam, &it)
                            : NEWTON_UNREALIZABLE;
   cnt->iters += it;
   cnt->calls += 1;
@@ -416,15 +430,25 @@ __device__ __forceinline__ void flush(unsigned long long* ctr, const Count& c) {
 
 __global__ void __launch_bounds__(B) step_kernel(StepArgs<double> a) {
   extern __shared__ __align__(16) double smem49[];
-  double* col = smem49 + threadIdx.x;
-  double* eq = smem49 + NP * B + threadIdx.x;
+  __shared__ double s_tab[EXPT_N];
+  __shared__ unsigned short s_queue[B * Q];  // (thread << 6) | velocity
+  __shared__ int s_count;
+  const int t = threadIdx.x;
+  if (t == 0) s_count = 0;
+  load_exptab(s_tab);  // includes a barrier
+  double* col = smem49 + t;
+  double* eq = smem49 + NP * B + t;
   const Params& pr = a.prm;
   const size_t ps = a.ps;
-  const int x = blockIdx.x * B + threadIdx.x, y = blockIdx.y;
+  const int x0 = blockIdx.x * B, y = blockIdx.y;
+  const int x = x0 + t;
+  const bool active = x < pr.nx;
   Count cnt;
-  if (x < pr.nx) {
-    const size_t k = (size_t)y * pr.nx + x;
-    const int code = a.nxt_in[k];
+  size_t k = 0;
+  int code = 0;
+  if (active) {
+    k = (size_t)y * pr.nx + x;
+    code = a.nxt_in[k];
     const int Upx = lat_ux(code), Upy = lat_uy(code);
     for (int i = 0; i < Q; ++i) {
       const int sx = x - vx(i) - Upx, sy = y - vy(i) - Upy;
@@ -435,16 +459,32 @@ __global__ void __launch_bounds__(B) step_kernel(StepArgs<double> a) {
         col[i * B] = a.pop_in[i * ps + ks];
         col[(Q + i) * B] = a.pop_in[(Q + i) * ps + ks];
       } else {
-        double fd, gd;
-        cnt.rec += 1;
-        cnt.rec_fail += rebuild(pr, a.mom_in, ps, i, Upx, Upy, sx, sy, &fd, &gd, eq, &cnt);
-        col[i * B] = fd;
-        col[(Q + i) * B] = gd;
+        s_queue[atomicAdd(&s_count, 1)] = (unsigned short)((t << 6) | i);
       }
     }
+  }
+  __syncthreads();
+  // missing pulls, round-robin over the block; each thread solves in its own
+  // equilibrium column and writes into the owner's population column
+  const int nq = s_count;
+  for (int e = t; e < nq; e += B) {
+    const int owner = s_queue[e] >> 6, i = s_queue[e] & 63;
+    const int ox = x0 + owner;
+    const int ocode = a.nxt_in[(size_t)y * pr.nx + ox];
+    const int Upx = lat_ux(ocode), Upy = lat_uy(ocode);
+    double fd, gd;
+    cnt.rec += 1;
+    cnt.rec_fail += rebuild(pr, a.mom_in, ps, i, Upx, Upy, ox - vx(i) - Upx, y - vy(i) - Upy,
+                            &fd, &gd, eq, s_tab, &cnt);
+    smem49[i * B + owner] = fd;
+    smem49[(Q + i) * B + owner] = gd;
+  }
+  __syncthreads();
+  if (active) {
     uint8_t nb[8];
     if (pr.overlap > 0.0 && pr.rule == 1) neighbours(pr, a.nxt_in, x, y, nb);
-    collide(pr, col, eq, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, nb, &cnt);
+    collide(pr, col, eq, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, nb, s_tab,
+            &cnt);
   }
   flush(a.ctr, cnt);
 }
@@ -473,6 +513,8 @@ __device__ __forceinline__ void prim(const InitArgs49& a, size_t k, double* r, d
 // initial fields, then the first collision.
 __global__ void __launch_bounds__(B) init_kernel(InitArgs49 a) {
   extern __shared__ __align__(16) double smem49[];
+  __shared__ double s_tab[EXPT_N];
+  load_exptab(s_tab);
   double* col = smem49 + threadIdx.x;
   double* eq = smem49 + NP * B + threadIdx.x;
   const Params& pr = a.prm;
@@ -503,7 +545,7 @@ __global__ void __launch_bounds__(B) init_kernel(InitArgs49 a) {
     const bool ok = (r > 0.0) && (T > 0.0) && isfinite(r) && isfinite(T);
     double lam[M];
     int it = 0;
-    const int ns = ok ? newton13(ux - U0x, uy - U0y, T, pr.tol, pr.maxit, eq, lam, &it)
+    const int ns = ok ? newton13(ux - U0x, uy - U0y, T, pr.tol, pr.maxit, eq, s_tab, lam, &it)
                       : NEWTON_UNREALIZABLE;
     if (!ok) bad += 1;
     if (ok && ns != NEWTON_OK) cnt.fail += 1;
@@ -531,7 +573,8 @@ __global__ void __launch_bounds__(B) init_kernel(InitArgs49 a) {
                                         select_shift(a.rhouy[kk] / rr, pr.n0, pr.umax));
           }
       }
-      collide(pr, col, eq, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, nb, &cnt);
+      collide(pr, col, eq, code, k, a.ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, nb, s_tab,
+              &cnt);
     } else {
       for (int i = 0; i < NP; ++i) a.pop_out[i * a.ps + k] = 0.0;
       a.mom_out[k] = r;
@@ -553,6 +596,8 @@ __global__ void __launch_bounds__(B)
                        int n, double tol, int maxit, double* feq, double* lambda, int* iters,
                        int* status) {
   __shared__ double s_eq[Q * B];
+  __shared__ double s_tab[EXPT_N];
+  load_exptab(s_tab);
   const int k = blockIdx.x * B + threadIdx.x;
   if (k >= n) return;
   double* eq = s_eq + threadIdx.x;
@@ -560,7 +605,7 @@ __global__ void __launch_bounds__(B)
   int it = 0;
   const double r = rho[k];
   const int st = (r > 0.0 && isfinite(r))
-                     ? newton13(ubx[k], uby[k], T[k], tol, maxit, eq, lam, &it)
+                     ? newton13(ubx[k], uby[k], T[k], tol, maxit, eq, s_tab, lam, &it)
                      : NEWTON_UNREALIZABLE;
   for (int i = 0; i < Q; ++i) feq[(size_t)k * Q + i] = st == NEWTON_OK ? r * eq[i * B] : 0.0;
   for (int j = 0; j < M; ++j) lambda[(size_t)k * M + j] = st == NEWTON_OK ? lam[j] : 0.0;
