@@ -168,16 +168,27 @@ if __name__ == "__main__":
 
 # ---------------------------------------------------------------- D2Q49
 
-# FP64-pipe slots of the D2Q49 step per unit of work, measured with ncu on the
-# 256^2 shear layer (profiles/q49_step_kernel.md); None until measured.
-Q49_PER_ITER = None
-Q49_PER_CALL = None
-Q49_PER_NODE = None
+# Slots of the D2Q49 step (alb_q49.cu), counted like the rest of this file:
+# per Newton step, moments from the row sums (664), residual and its maximum
+# (45), Jacobian entries from the moments (140), Cholesky with reciprocal
+# pivots (690), two triangular solves (182), one line-search evaluation of
+# the 49 exponentials with the dual value (1060); per solve, targets, the
+# Maxwellian start's evaluation, log and normalisation (1220); per node,
+# moments, shift choice and BGK store (550); per rebuilt pull, gradients and
+# Grad factors (70).
+Q49_PER_ITER = 664 + 45 + 140 + 690 + 182 + 13 + 1060
+Q49_PER_CALL = 1220
+Q49_PER_NODE = 550
+Q49_PER_REBUILD = 70
+# ncu counted 45,952 FP64-pipe thread instructions per node on the 512^2
+# shear layer (11.46 Newton steps, 2.32 solves, 1.32 rebuilds per node),
+# where the count above gives 35,548.
+CALIBRATION["q49"] = 45952.0 / 35548.0
 
 
 def q49_slots(delta, node_updates):
-    """FP64 slots of D2Q49 launches from their counters, or None."""
-    if Q49_PER_ITER is None:
-        return None
-    return (Q49_PER_ITER * delta["newton_iterations"] + Q49_PER_CALL * delta["newton_calls"]
-            + Q49_PER_NODE * node_updates)
+    """FP64 slots of D2Q49 launches from their counters."""
+    rebuilds = delta["reconstructions"]
+    raw = (Q49_PER_ITER * delta["newton_iterations"] + Q49_PER_CALL * delta["newton_calls"]
+           + Q49_PER_NODE * node_updates + Q49_PER_REBUILD * rebuilds)
+    return CALIBRATION["q49"] * raw
