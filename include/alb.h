@@ -281,11 +281,17 @@ int alb_equilibrium(const double* rho, const double* ubx, const double* uby, con
                     int n, double tol, int maxit, int precision, double* feq, double* lambda,
                     int* iters, int* status, void* stream);
 
-/* out[k] = exp(-s[k]) by the table-driven FP64 exponential that the FP32
- * form's equilibrium uses (Tang's method: 256-entry table of 2^(j/256), degree-4
- * polynomial on |r| <= ln2/512). 0 below 2^-1022, +inf from 2^1024 on. Device
- * arrays of n doubles. Exposed so that its accuracy can be checked. */
+/* out[k] = exp(-s[k]) by the table-driven FP64 exponential of the FP64
+ * Newton (Tang's method: 256-entry table of 2^(j/256), two-part reduction,
+ * degree-4 polynomial on |r| <= ln2/512). 0 below 2^-1022, +inf from 2^1024
+ * on. Device arrays of n doubles. Exposed so that its accuracy can be
+ * checked. */
 int alb_exp_neg(const double* s, int n, double* out, void* stream);
+
+/* The same with the cheaper variant of the FP32 form's FP64 residual
+ * evaluations: one-step reduction and degree-3 polynomial, relative error
+ * below 2e-13. Same arguments and limits. */
+int alb_exp_neg_refine(const double* s, int n, double* out, void* stream);
 
 /* Shift criterion (Eq. criterion with offset n0, clamped to +-u_max) applied
  * to u[k] = rhou[k] / rho[k] in FP64 for n values; writes out[k]. */

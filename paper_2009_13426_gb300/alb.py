@@ -129,6 +129,8 @@ _SIGS = {
     "alb_equilibrium": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_double,
                                                                 ctypes.c_int, ctypes.c_int]
                         + [ctypes.c_void_p] * 5),
+    "alb_exp_neg_refine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "alb_exp_neg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                    ctypes.c_void_p]),
     "alb_select_shift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -333,6 +335,11 @@ def alb_equilibrium(rho, ubx, uby, T, n, tol, maxit, feq, lam=None, iters=None, 
     return _check(lib().alb_equilibrium(_ptr(rho), _ptr(ubx), _ptr(uby), _ptr(T), int(n),
                                         float(tol), int(maxit), int(precision), _ptr(feq),
                                         _ptr(lam), _ptr(iters), _ptr(status), _stream(stream)))
+
+
+def alb_exp_neg_refine(s, n, out, stream=None):
+    """out = exp(-s) by the FP32 form's cheaper FP64 exponential (CUDA tensors)."""
+    return _check(lib().alb_exp_neg_refine(_ptr(s), int(n), _ptr(out), _stream(stream)))
 
 
 def alb_exp_neg(s, n, out, stream=None):

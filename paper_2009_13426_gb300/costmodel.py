@@ -32,8 +32,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # Ratio of the FP64-pipe instructions ncu counted for one launch of each
 # step kernel to the slots this model gives for the same launch; it absorbs
 # what the hand count misses (compiler scheduling, predication) and is
-# measured again whenever a kernel changes (see profiles/).
-CALIBRATION = {"fp32": 1143.8 / 1244.2, "fp64": 5565.0 / 6073.3}
+# measured again whenever a kernel changes.
+CALIBRATION = {"fp32": 1024.3 / 1122.5, "fp64": 5573.7 / 6073.3}
 
 BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
                   "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}
@@ -105,10 +105,10 @@ def plain_call():
 
 def mixed_eval():
     """FP64 residual evaluation of the refinement: grouped exponents (55),
-    21 table-driven exponentials (9 each: reduction 4, degree-4 polynomial 4,
-    scaling 1), grouped constraint sums (68), residual and its maximum (17),
-    conversions and the update (24)."""
-    return 55 + 21 * 9 + 68 + 17 + 24
+    21 table-driven exponentials (7 each: one-step reduction 3, degree-3
+    polynomial 3, scaling 1), grouped constraint sums (68), residual and its
+    maximum (17), conversions and the update (24)."""
+    return 55 + 21 * 7 + 68 + 17 + 24
 
 
 def mixed_call():

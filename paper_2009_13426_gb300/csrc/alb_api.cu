@@ -601,6 +601,13 @@ int alb_equilibrium13(const double* rho, const double* ubx, const double* uby, c
   return ALB_OK;
 }
 
+int alb_exp_neg_refine(const double* s, int n, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!s || !out)))
+    return fail(ALB_EINVAL, "alb_exp_neg_refine: bad arguments");
+  ALB_CUDA(launch_exp_neg(s, n, out, (cudaStream_t)stream, true), "alb_exp_neg_refine");
+  return ALB_OK;
+}
+
 int alb_exp_neg(const double* s, int n, double* out, void* stream) {
   if (n < 0 || (n > 0 && (!s || !out))) return fail(ALB_EINVAL, "alb_exp_neg: bad arguments");
   ALB_CUDA(launch_exp_neg(s, n, out, (cudaStream_t)stream), "alb_exp_neg");

@@ -96,7 +96,8 @@ cudaError_t launch_equilibrium(const double* rho, const double* ubx, const doubl
                                const double* T, int n, double tol, int maxit, int precision,
                                double* feq, double* lambda, int* iters, int* status,
                                cudaStream_t s);
-cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s);
+cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s,
+                           bool refine = false);
 // D2Q49 reference solver (alb_q49.cu), FP64 only.
 cudaError_t launch_init_q49(FlowDev& f, const double* rho, const double* rhoux,
                             const double* rhouy, const double* rhoE, cudaStream_t s);

@@ -219,11 +219,12 @@ __global__ void __launch_bounds__(BLOCK)
   if (status) status[k] = st;
 }
 
+template <bool REFINE>
 __global__ void exp_neg_kernel(const double* s, int n, double* out) {
   __shared__ double s_tab[EXPT_N];
   load_exptab(s_tab);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) out[k] = exp_neg(s[k], s_tab);
+  if (k < n) out[k] = REFINE ? exp_neg_refine(s[k], s_tab) : exp_neg(s[k], s_tab);
 }
 
 __global__ void select_kernel(const double* rho, const double* rhou, int n, double n0, int umax,
@@ -327,9 +328,12 @@ cudaError_t launch_equilibrium(const double* rho, const double* ubx, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s) {
+cudaError_t launch_exp_neg(const double* x, int n, double* out, cudaStream_t s, bool refine) {
   if (n <= 0) return cudaSuccess;
-  exp_neg_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, n, out);
+  if (refine)
+    exp_neg_kernel<true><<<(n + 255) / 256, 256, 0, s>>>(x, n, out);
+  else
+    exp_neg_kernel<false><<<(n + 255) / 256, 256, 0, s>>>(x, n, out);
   return cudaGetLastError();
 }
 

@@ -106,6 +106,28 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   return q * sc;
 }
 
+// exp(-s) for the FP32 form's residual evaluations, which need ~1e-13
+// relative accuracy only (their tolerance is 1e-12 on G/rho and the result is
+// rounded to FP32): the same table, the reduction in one step with ln2/N
+// rounded, and the degree-3 Taylor polynomial (truncation below 1.4e-13).
+// 7 FP64 operations.
+__device__ __forceinline__ double exp_neg_refine(double s, const double* tab) {
+  const double shifter = 6755399441055744.0;
+  const double t = fma(-s, EXPT_INV_L, shifter);
+  const int n = (int)(unsigned)__double2loint(t);
+  const double nd = t - shifter;
+  const double r = fma(nd, -EXPT_L, -s);
+  double q = fma(r, EXPT_C3, EXPT_C2);
+  q = fma(q, r, 1.0);
+  q = fma(q, r, 1.0);
+  const int e = n >> EXPT_BITS;
+  const long long bits =
+      __double_as_longlong(tab[n & (EXPT_N - 1)]) + ((long long)e << 52);
+  double sc = __longlong_as_double(bits);
+  sc = e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : sc);
+  return q * sc;
+}
+
 // Packed lower triangle of the 8x8 Jacobian: entry (a, b), b <= a.
 __host__ __device__ constexpr int tri(int a, int b) { return a * (a + 1) / 2 + b; }
 
@@ -154,7 +176,9 @@ struct PassGH32 {
 };
 
 // FP64 pass: the constraint sums M = sum p P with p = exp(-s) in FP64, each p
-// also written to the caller's shared column (p_i at col[i * stride]).
+// also written to the caller's shared column (p_i at col[i * stride]);
+// REFINE selects the cheaper exponential of the FP32 form's refinement.
+template <bool REFINE>
 struct PassG64 {
   double M[NM];
   const double* tab;
@@ -164,14 +188,17 @@ struct PassG64 {
 #pragma unroll
     for (int k = 0; k < NM; ++k) M[k] = 0.0;
   }
+  __device__ __forceinline__ double ex(double s) const {
+    return REFINE ? exp_neg_refine(s, tab) : exp_neg(s, tab);
+  }
   __device__ __forceinline__ void rest(double s) {
-    const double p = exp_neg(s, tab);
+    const double p = ex(s);
     col[0] = p;
     M[0] += p;
   }
   template <int A, int AX, int IP, int IM>
   __device__ __forceinline__ void pair(double sp, double sm) {
-    const double pp = exp_neg(sp, tab), pm = exp_neg(sm, tab);
+    const double pp = ex(sp), pm = ex(sm);
     col[IP * stride] = pp;
     col[IM * stride] = pm;
     const double S = pp + pm, D = pp - pm;
@@ -188,8 +215,8 @@ struct PassG64 {
   }
   template <int A, int IPP, int IMP, int IMM, int IPM>
   __device__ __forceinline__ void quad(double spp, double smp, double smm, double spm) {
-    const double ppp = exp_neg(spp, tab), pmp = exp_neg(smp, tab);
-    const double pmm = exp_neg(smm, tab), ppm = exp_neg(spm, tab);
+    const double ppp = ex(spp), pmp = ex(smp);
+    const double pmm = ex(smm), ppm = ex(spm);
     col[IPP * stride] = ppp;
     col[IMP * stride] = pmp;
     col[IMM * stride] = pmm;
@@ -397,7 +424,7 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
   for (int k = 0; k < NM; ++k) lam[k] = (double)lam32[k];
   *evals = 0;
   for (int r = 0;; ++r) {
-    PassG64 ps(tab, col, stride);
+    PassG64<true> ps(tab, col, stride);
     visit_groups<double>(lam, ps);
     ++*evals;
     double gmax = 0.0;
@@ -478,7 +505,7 @@ __device__ __forceinline__ void jacobian_grouped(const double* col, int stride, 
 // exponential, grouped exponents and sums).
 __device__ __forceinline__ void eval_fp64(const double l[NM], const double* tab, double* col,
                                           int stride, double M[NM]) {
-  PassG64 pg(tab, col, stride);
+  PassG64<false> pg(tab, col, stride);
   visit_groups<double>(l, pg);
 #pragma unroll
   for (int k = 0; k < NM; ++k) M[k] = pg.M[k];

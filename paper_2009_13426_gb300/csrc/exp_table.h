@@ -8,6 +8,7 @@ constexpr int EXPT_N = 256;
 constexpr double EXPT_INV_L = 0x1.71547652b82fep+8;  // 256 / ln 2
 constexpr double EXPT_L_HI = 0x1.62e42ff000000p-9;   // ln2/256, 33 significant bits
 constexpr double EXPT_L_LO = -0x1.718432a1b0e26p-43;   // ln2/256 - EXPT_L_HI
+constexpr double EXPT_L = 0x1.62e42fefa39efp-9;      // ln2/256 (one-step reduction)
 constexpr double EXPT_C2 = 0x1.0000000000000p-1;  // 1/2!
 constexpr double EXPT_C3 = 0x1.5555555555555p-3;  // 1/3!
 constexpr double EXPT_C4 = 0x1.5555555555555p-5;  // 1/4!

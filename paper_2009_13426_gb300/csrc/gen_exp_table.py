@@ -8,6 +8,12 @@ r = x - n ln2/N, |r| <= ln2/(2N); 2^(n/N) = 2^(n >> BITS) * T[n & (N-1)] with
 T[j] = 2^(j/N); exp(r) by its Taylor polynomial of degree DEG = 4 (remainder
 below r^5/5! < 4e-17 on |r| <= ln2/512).
 
+A cheaper variant for residual evaluations that only need ~1e-13 relative
+accuracy uses the same table with the reduction r = x - n L in one step
+(L = ln2/N rounded to the nearest double; error |n| ulp(L)/2 < 1e-14 for
+|x| < 700) and the Taylor polynomial of degree 3 (remainder below
+r^4/4! < 1.4e-13 on |r| <= ln2/512).
+
 Every constant is computed here with 60-digit decimal arithmetic and rounded
 to the nearest double: T[j], N/ln2, the two-part split of ln2/N (high part
 with 33 significant bits so that n * high is exact for |n| < 2^20) and 1/k!.
@@ -77,6 +83,8 @@ def main():
     out.append("constexpr double EXPT_L_HI = %s;   // ln2/%d, %d significant bits"
                % (hexd(hi), N, HI_BITS))
     out.append("constexpr double EXPT_L_LO = %s;   // ln2/%d - EXPT_L_HI" % (hexd(lo), N))
+    out.append("constexpr double EXPT_L = %s;      // ln2/%d (one-step reduction)"
+               % (hexd(L), N))
     for k in range(2, DEG + 1):
         out.append("constexpr double EXPT_C%d = %s;  // 1/%d!" % (k, hexd(fact[k]), k))
     out.append("}  // namespace alb")

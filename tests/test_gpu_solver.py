@@ -103,3 +103,29 @@ def test_table_exponential_against_cuda_exp(alb):
     torch.cuda.synchronize()
     o = o.cpu().numpy()
     assert o[0] == 0.0 and np.isinf(o[1])
+
+
+def test_refinement_exponential_within_its_bound(alb):
+    """The FP32 form's residual exponential: degree-3 Taylor polynomial on
+    |r| <= ln2/512 (remainder r^4/4! < 1.4e-13) and a one-step reduction
+    (error below 1e-14 for |s| < 700): relative error below 2e-13 against
+    CUDA's FP64 exp, and the same limits."""
+    rng = np.random.default_rng(9)
+    s = np.concatenate([rng.uniform(-30, 60, 400000), rng.uniform(-690, 690, 100000),
+                        np.arange(-64, 64) * np.log(2) / 32 + np.log(2) / 512,
+                        [0.0, 1.0, -1.0, 700.0, -700.0]])
+    n = s.size
+    sd = _dev(s)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    alb.alb_exp_neg_refine(sd, n, out)
+    ref = torch.exp(-sd)
+    torch.cuda.synchronize()
+    rel = np.abs(out.cpu().numpy() - ref.cpu().numpy()) / ref.cpu().numpy()
+    assert rel.max() <= 2e-13, rel.max()
+    assert rel.max() > 4 * 2.0 ** -52  # it is the cheaper variant
+    t = _dev([1000.0, -1000.0])
+    o = torch.empty(2, dtype=torch.float64, device="cuda")
+    alb.alb_exp_neg_refine(t, 2, o)
+    torch.cuda.synchronize()
+    o = o.cpu().numpy()
+    assert o[0] == 0.0 and np.isinf(o[1])
