@@ -163,6 +163,41 @@ def test_grad_stress_term_exact_at_rest():
     assert abs(((f1 - f0) * x * x).sum()) < 1e-15 and abs((g1 - g0).sum()) < 1e-15
 
 
+@pytest.mark.parametrize("gamma", [1.4, 2.0])
+@pytest.mark.parametrize("T", [0.6, 1.0])
+def test_grad_heat_flux_term_exact_at_rest(gamma, T):
+    """At rest with only a temperature gradient, Eqs. GradGeneral_f/_g give
+    f - f^eq = f^eq q.xi/(rho Cp T^2) (|xi|^2/(2T) - Cp) and g - g^eq =
+    g^eq 2 q.xi/(rho Cp), q = -kappa grad T, kappa = rho Cp nu. Their
+    momentum and heat flux are then fixed by the equilibrium's moments
+    M2, M4, M6 = sum f^eq xi_x^2 |xi|^{0,2,4} (symmetric lattice at rest):
+    momentum q (M4/(2T) - Cp M2) / (rho Cp T^2), heat flux
+    q [(M6/(2T) - Cp M4) / (2 rho Cp T^2) + (2 Cv - 2) T M2 / (rho Cp)];
+    no mass and no energy. This pins the sign of q, kappa, and every factor
+    of the two heat-flux terms."""
+    nu, rho = 0.05, 1.1
+    cv = 1.0 / (gamma - 1.0)
+    cp = gamma * cv
+    cfg = O.make_config(4, 4, nu=nu, gamma=gamma)
+    dT = np.array([0.02, -0.013])
+    st, f1, g1 = O.grad_populations(cfg, 0, 0, rho, 0.0, 0.0, T, np.zeros((2, 2)), dT, 1.0)
+    st, f0, g0 = O.grad_populations(cfg, 0, 0, rho, 0.0, 0.0, T, np.zeros((2, 2)), 0 * dT, 1.0)
+    assert st == O.OK
+    x, y = _xi()
+    c2 = x * x + y * y
+    M2, M4, M6 = (f0 * x * x).sum(), (f0 * x * x * c2).sum(), (f0 * x * x * c2 * c2).sum()
+    q = -rho * cp * nu * dT
+    df, dg = f1 - f0, g1 - g0
+    k_mom = (M4 / (2 * T) - cp * M2) / (rho * cp * T * T)
+    k_q = (M6 / (2 * T) - cp * M4) / (2 * rho * cp * T * T) + (2 * cv - 2) * T * M2 / (rho * cp)
+    tol = 1e-13 * np.abs(q).max()
+    assert abs(df.sum()) < tol and abs(dg.sum()) < tol
+    assert abs(0.5 * (c2 * df + dg).sum()) < tol
+    for a, xa in ((0, x), (1, y)):
+        assert abs((df * xa).sum() - q[a] * k_mom) < tol
+        assert abs(0.5 * (xa * (c2 * df + dg)).sum() - q[a] * k_q) < tol
+
+
 # ---------------------------------------------------------------- streaming
 
 def _smooth(n, ux0=0.0, uy0=0.0):
