@@ -18,8 +18,10 @@
  *        reconstruction (Eqs. GradGeneral, GradGeneral_f, GradGeneral_g) with
  *        second-order central differences of u and T at the sender.
  *
- * Parity status of each function is given beside it and in the repository's
- * design notes.
+ * Every function here is pinned by tests/test_oracle_*.py against what the
+ * paper and the mathematics fix (closed forms, exact rational arithmetic,
+ * Gauss-Hermite moments, the paper's printed values, an exact Riemann
+ * solver); none is unpinned.
  */
 #ifndef ALB_ORACLE_H
 #define ALB_ORACLE_H
