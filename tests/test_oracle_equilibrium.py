@@ -272,3 +272,46 @@ def test_reduced_model_differs_from_eight_moments_away_from_rest():
     x, y = _xi()
     assert abs((f8 * x * x).sum() - rho * (ubx ** 2 + T)) < 1e-11
     assert abs((f4 * x * x).sum() - rho * (ubx ** 2 + T)) > 1e-4
+
+
+def _deviations(U, u, T=0.7):
+    """Fig. 3 quantities for lattice U at velocity u (flow along x, rho = 1):
+    the relative deviations of the unconstrained third-order moment M_xxx and
+    of the fourth-order trace M_xxaa from their Maxwellian values (Sec.
+    II.C.2), or None where the root finder does not converge."""
+    st, lam, feq, _ = O.equilibrium(1.0, u - U, 0.0, T)
+    if st != O.OK:
+        return None
+    x, y = _xi()
+    cx = x + U
+    E = 0.5 * (u * u + 2 * T)
+    m30, M30 = (feq * cx ** 3).sum(), u * (u * u + 3 * T)
+    m4, M4 = (feq * cx * cx * (cx * cx + y * y)).sum(), 2 * ((E + 2 * T) * u * u + T * (E + T))
+    return abs(M30 - m30) / abs(M30), abs(M4 - m4) / abs(M4)
+
+
+def test_macroscopic_deviation_and_shift_overlap():
+    """Sec. II.C.2 / Fig. 3 (D2Q21, M = 8, T = 0.7, flow along x): the
+    deviations stay under the 10 % threshold over each shifted lattice's own
+    range, and the velocity ranges where neighbouring shifts converge with
+    deviations under 10 % overlap widely (here over more than one unit of
+    velocity), which is what lets the lattice change without interpolation.
+    M_xxx is checked for u >= 0.3 only: it vanishes at u = 0, where its
+    relative deviation has no meaning."""
+    grid = np.round(np.arange(0.3, 3.96, 0.05), 2)
+
+    def ok(U, u):
+        d = _deviations(U, u)
+        return d is not None and d[0] < 0.1 and d[1] < 0.1
+
+    good = {U: {u for u in grid if ok(U, u)} for U in (0, 1, 2)}
+    for U in (0, 1, 2):
+        own = [u for u in grid if U - 0.5 < u <= U + 0.5]
+        assert own and all(u in good[U] for u in own), U
+    for U in (0, 1):
+        both = sorted(good[U] & good[U + 1])
+        assert both[-1] - both[0] >= 1.0, (U, both[0], both[-1])
+    # the convergence range moves with the shift: lattice U converges up to
+    # about U + 1.95 (the operability edge of the unshifted lattice, + U)
+    for U in (0, 1, 2):
+        assert _deviations(U, U + 1.95) is not None and _deviations(U, U + 2.05) is None
