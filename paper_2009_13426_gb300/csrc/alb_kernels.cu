@@ -61,7 +61,8 @@ __device__ __forceinline__ void init_prim(const double* rho, const double* rhoux
 // Grad-regularised initial condition (Sec. IV.A.1): h = h^eq (1 + phi_h) in the
 // lattice chosen from the initial velocity, then the first collision.
 template <typename P>
-__global__ void __launch_bounds__(BLOCK) init_kernel(InitArgs<P> a) {
+__global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1))
+    init_kernel(InitArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_tab[EXPT_N];
   load_exptab(s_tab);
