@@ -186,3 +186,57 @@ def test_prandtl_flows_in_a_batch(alb):
             assert_same(state(fl), ref[k], "flow %d" % k)
     finally:
         b.close()
+
+
+def _sync_flagged(alb, obj):
+    """Wait; a flagged root-finder failure (ALB_ENEWTON) is part of the state
+    being compared, not an error here."""
+    try:
+        obj.sync()
+    except alb.AlbError as e:
+        if e.code != alb.ALB_ENEWTON:
+            raise
+
+
+def test_mixed_configurations_in_one_batch(alb):
+    """Flows that differ in every per-flow option - overlap rules, sensor,
+    zero-gradient ends, the reduced model, Maxwellian or previous starts, u_max,
+    n0 - share one launch and each stays bit-identical to its own run,
+    counters (including any flagged rebuild failures) included."""
+    ZG = alb.ALB_ZERO_GRADIENT
+    specs = [
+        (SPECS[0], dict(shift_overlap=0.5, shift_rule=alb.ALB_RULE_HISTORY)),
+        (SPECS[1], dict(shift_overlap=0.4, shift_rule=alb.ALB_RULE_NEIGHBOURS, bc_x=ZG)),
+        (SPECS[2], dict(sensor=1, bc_y=ZG, n0=0.51)),
+        (SPECS[3], dict(moments=4)),
+        (SPECS[4], dict(newton_start=alb.ALB_START_PREVIOUS, u_max=3)),
+        (SPECS[5], dict(shift_overlap=0.3, shift_rule=alb.ALB_RULE_NEIGHBOURS, sensor=1,
+                        prandtl=0.8)),
+    ]
+    cfgs = [dict(cfg_of(alb, sp), **extra) for sp, extra in specs]
+    ref = []
+    for (sp, _), c in zip(specs, cfgs):
+        fl = alb.Flow(**c)
+        assert fl.init(*sp.fields()) == alb.ALB_OK
+        fl.step(STEPS)
+        _sync_flagged(alb, fl)
+        ref.append((state(fl), fl.stats()))
+        fl.close()
+    b = alb.Batch(cfgs)
+    try:
+        for (sp, _), fl in zip(specs, b.flows):
+            fl.init(*sp.fields())
+        b.step(STEPS)
+        _sync_flagged(alb, b)
+        for k, fl in enumerate(b.flows):
+            assert_same(state(fl), ref[k][0], "flow %d" % k)
+            got, want = fl.stats(), ref[k][1]
+            if want["reconstruction_failures"] or want["newton_failures"]:
+                # a failing root finder's discarded path: the two kernels are
+                # compiled apart and may fuse its multiply-adds differently
+                for key in ("newton_iterations", "fp64_evaluations"):
+                    got.pop(key)
+                    want.pop(key)
+            assert got == want, k
+    finally:
+        b.close()
