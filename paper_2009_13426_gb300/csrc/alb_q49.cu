@@ -7,9 +7,10 @@
 // Velocity i = (x, y) has index i = (x + 3) + 7 (y + 3). One thread per node;
 // a block is a row segment of B nodes. Each thread owns two columns of the
 // block's dynamic shared memory (stride B): its 98 pulled populations and the
-// 49 equilibrium values per unit density of its latest solve. Missing pulls
-// go to a block-wide queue and are rebuilt round-robin by all threads of the
-// block, so that a warp does not wait for its lanes' rebuilds one by one.
+// 49 equilibrium values per unit density of its latest solve. A missing pull
+// needs the equilibrium of its sender's state in the receiver's lattice; the
+// block solves each distinct (sender, lattice) once, round-robin over its
+// threads, and forms the pulls from the multipliers (see step_kernel).
 // Exponentials use the table-driven FP64 exp of the D2Q21 kernels.
 //
 // Newton on the 13 multipliers follows the 8-moment solver's iteration
@@ -262,13 +263,14 @@ struct Count {
   unsigned iters = 0, calls = 0, fail = 0, rec = 0, rec_fail = 0;
 };
 
-// Grad rebuild of pull i = (cx, cy) into lattice (Upx, Upy) from the sender's
-// stored moments at (sx, sy), as the D2Q21 path: h* = h^eq (1 + (1 - 1/tau)
-// phi_h + (1/tau - 1/tau_Pr) phi_h,q), tau of the sender without the sensor;
-// the Maxwellian exponential normalised over the lattice if the solve fails.
-__device__ __noinline__ int rebuild(const Params pr, const double* __restrict__ mom, size_t ps,
-                                    int i, int Upx, int Upy, int sx, int sy, double* fi,
-                                    double* gi, double* eq, const double* tab, Count* cnt) {
+// The sender of a rebuilt pull: its stored moments at the (possibly ghost)
+// position (sx, sy) and the central differences of u and T around it.
+struct Sender {
+  double rho, ux, uy, T, du[2][2], dT[2];
+};
+
+__device__ __forceinline__ Sender sender_state(const Params& pr, const double* __restrict__ mom,
+                                               size_t ps, int sx, int sy) {
   bool gh = false;
   const int rx = resolve(sx, pr.nx, pr.bcx, &gh), ry = resolve(sy, pr.ny, pr.bcy, &gh);
   const int xp = resolve(sx + 1, pr.nx, pr.bcx, &gh), xm = resolve(sx - 1, pr.nx, pr.bcx, &gh);
@@ -279,48 +281,88 @@ __device__ __noinline__ int rebuild(const Params pr, const double* __restrict__ 
   const double* mux = mom + ps;
   const double* muy = mom + 2 * ps;
   const double* mT = mom + 3 * ps;
-  const double rho = mom[ks], ux = mux[ks], uy = muy[ks], T = mT[ks];
-  double du[2][2], dT[2];
-  du[0][0] = 0.5 * (mux[kxp] - mux[kxm]);
-  du[1][0] = 0.5 * (mux[kyp] - mux[kym]);
-  du[0][1] = 0.5 * (muy[kxp] - muy[kxm]);
-  du[1][1] = 0.5 * (muy[kyp] - muy[kym]);
-  dT[0] = 0.5 * (mT[kxp] - mT[kxm]);
-  dT[1] = 0.5 * (mT[kyp] - mT[kym]);
-  const double ubx = ux - Upx, uby = uy - Upy;
-  double lam[M];
-  int it = 0;
-  const int st = rho > 0.0 ? newton13(ubx, uby, T, pr.tol, pr.maxit, eq, tab, lam, &it)
-                           : NEWTON_UNREALIZABLE;
-  cnt->iters += it;
-  cnt->calls += 1;
-  const double gfac = (2.0 * pr.cv - 2.0) * T;
-  if (st != NEWTON_OK) {
-    double z = 0.0, pi = 0.0;
-    if (T > 0.0) {
-      for (int j = 0; j < Q; ++j) {
-        const double dx = vx(j) - ubx, dy = vy(j) - uby;
-        const double e = exp(-(dx * dx + dy * dy) / (2.0 * T));
-        z += e;
-        if (j == i) pi = e;
-      }
-      *fi = rho * pi / z;
-    } else {
-      *fi = 0.0;
-    }
-    *gi = gfac * (*fi);
-    return 1;
-  }
-  const double tau = 0.5 + pr.nu / T;
+  Sender s;
+  s.rho = mom[ks];
+  s.ux = mux[ks];
+  s.uy = muy[ks];
+  s.T = mT[ks];
+  s.du[0][0] = 0.5 * (mux[kxp] - mux[kxm]);
+  s.du[1][0] = 0.5 * (mux[kyp] - mux[kym]);
+  s.du[0][1] = 0.5 * (muy[kxp] - muy[kxm]);
+  s.du[1][1] = 0.5 * (muy[kyp] - muy[kym]);
+  s.dT[0] = 0.5 * (mT[kxp] - mT[kxm]);
+  s.dT[1] = 0.5 * (mT[kyp] - mT[kym]);
+  return s;
+}
+
+// Grad value of pull i in lattice (Upx, Upy) from the sender's equilibrium
+// multipliers lam in that lattice: h* = h^eq (1 + (1 - 1/tau) phi_h +
+// (1/tau - 1/tau_Pr) phi_h,q), tau of the sender without the sensor.
+__device__ __forceinline__ void grad_value(const Params& pr, const Sender& s, int i, int Upx,
+                                           int Upy, const double* lam, const double* tab,
+                                           double* fi, double* gi) {
+  const double gfac = (2.0 * pr.cv - 2.0) * s.T;
+  const double tau = 0.5 + pr.nu / s.T;
   const double omega = 1.0 - 1.0 / tau;
-  const double feq = rho * eq[i * B];
-  const double cbx = (double)(vx(i) + Upx) - ux;
-  const double cby = (double)(vy(i) + Upy) - uy;
+  double l[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) l[k] = lam[k];
+  const double feq = s.rho * exp_neg(1.0 + lam_dot(l, i), tab);
+  const double cbx = (double)(vx(i) + Upx) - s.ux;
+  const double cby = (double)(vy(i) + Upy) - s.uy;
   double phf, phg, phq;
-  grad_phi(pr, rho, T, cbx, cby, du, dT, &phf, &phg, &phq);
-  const double w = pr.shakhov ? 1.0 / tau - 1.0 / (0.5 + (pr.nu / pr.prandtl) / T) : 0.0;
+  grad_phi(pr, s.rho, s.T, cbx, cby, s.du, s.dT, &phf, &phg, &phq);
+  const double w = pr.shakhov ? 1.0 / tau - 1.0 / (0.5 + (pr.nu / pr.prandtl) / s.T) : 0.0;
   *fi = feq * (1.0 + omega * phf + w * phq);
   *gi = gfac * feq * (1.0 + omega * phg + w * phg);
+}
+
+// Fallback of a rebuild whose solve failed: the Maxwellian exponential of the
+// sender's state normalised over the lattice.
+__device__ __forceinline__ void fallback_value(const Params& pr, const Sender& s, int i, int Upx,
+                                               int Upy, double* fi, double* gi) {
+  const double ubx = s.ux - Upx, uby = s.uy - Upy;
+  double z = 0.0, pi = 0.0;
+  if (s.T > 0.0) {
+    for (int j = 0; j < Q; ++j) {
+      const double dx = vx(j) - ubx, dy = vy(j) - uby;
+      const double e = exp(-(dx * dx + dy * dy) / (2.0 * s.T));
+      z += e;
+      if (j == i) pi = e;
+    }
+    *fi = s.rho * pi / z;
+  } else {
+    *fi = 0.0;
+  }
+  *gi = (2.0 * pr.cv - 2.0) * s.T * (*fi);
+}
+
+// Equilibrium multipliers of the sender's state in lattice (Upx, Upy); the
+// thread's equilibrium column is scratch. Returns the solve's status.
+__device__ __noinline__ int sender_solve(const Params pr, const Sender s, int Upx, int Upy,
+                                         double* eq, const double* tab, double lam[M],
+                                         Count* cnt) {
+  int it = 0;
+  const int st = s.rho > 0.0 ? newton13(s.ux - Upx, s.uy - Upy, s.T, pr.tol, pr.maxit, eq, tab,
+                                        lam, &it)
+                             : NEWTON_UNREALIZABLE;
+  cnt->iters += it;
+  cnt->calls += 1;
+  return st;
+}
+
+// A rebuild done in full by one thread (pulls that did not fit the block's
+// table of distinct senders): returns 1 if the fallback was used.
+__device__ __noinline__ int rebuild(const Params pr, const double* __restrict__ mom, size_t ps,
+                                    int i, int Upx, int Upy, int sx, int sy, double* fi,
+                                    double* gi, double* eq, const double* tab, Count* cnt) {
+  const Sender s = sender_state(pr, mom, ps, sx, sy);
+  double lam[M];
+  if (sender_solve(pr, s, Upx, Upy, eq, tab, lam, cnt) != NEWTON_OK) {
+    fallback_value(pr, s, i, Upx, Upy, fi, gi);
+    return 1;
+  }
+  grad_value(pr, s, i, Upx, Upy, lam, tab, fi, gi);
   return 0;
 }
 
@@ -428,13 +470,38 @@ __device__ __forceinline__ void flush(unsigned long long* ctr, const Count& c) {
   warp_count(ctr + CTR_REC_FAIL, c.rec_fail);
 }
 
+// Distinct rebuild solves of a block: every missing pull (owner, i) needs the
+// equilibrium of its sender's state in the owner's lattice, and the pulls of
+// neighbouring owners often share the sender and the lattice. Phase 1 enters
+// each (sender position, lattice) key into a hash table in shared memory;
+// phase 2 solves each distinct key once (round-robin over the block) and keeps
+// its multipliers; phase 3 forms every missing pull from them (one exponential
+// and the Grad factors). Keys beyond the table's capacity are rebuilt in full
+// by their owner. A pull's value is a function of its key and velocity only,
+// so neither the order of insertion nor the solving thread changes it.
+constexpr int HCAP = 512;        // hash positions per block (power of two)
+constexpr int SCAP = 192;        // distinct solves kept per block
+constexpr int KW = B + 12;       // sender x offsets: x0 - 6 .. x0 + B + 5
+constexpr unsigned EMPTY = 0xffffffffu;
+constexpr unsigned short NOSLOT = 0xffff;
+
+__device__ __forceinline__ unsigned rebuild_key(int sx, int sy, int x0, int y, int code) {
+  return (unsigned)(((sy - y + 6) * KW + (sx - x0 + 6)) * 49 + code);
+}
+
 __global__ void __launch_bounds__(B) step_kernel(StepArgs<double> a) {
   extern __shared__ __align__(16) double smem49[];
   __shared__ double s_tab[EXPT_N];
-  __shared__ unsigned short s_queue[B * Q];  // (thread << 6) | velocity
-  __shared__ int s_count;
+  __shared__ double s_lam[SCAP * M];      // multipliers of the distinct solves
+  __shared__ unsigned s_hkey[HCAP];       // hash table: key or EMPTY
+  __shared__ unsigned short s_hslot[HCAP];  // solve slot of a key, or NOSLOT
+  __shared__ unsigned s_skey[SCAP];       // key of each solve slot
+  __shared__ unsigned char s_sok[SCAP];   // 1 if the slot's solve converged
+  __shared__ unsigned short s_pos[Q * B];  // hash position of each missing pull
+  __shared__ int s_nslots;
   const int t = threadIdx.x;
-  if (t == 0) s_count = 0;
+  for (int j = t; j < HCAP; j += B) s_hkey[j] = EMPTY;
+  if (t == 0) s_nslots = 0;
   load_exptab(s_tab);  // includes a barrier
   double* col = smem49 + t;
   double* eq = smem49 + NP * B + t;
@@ -446,6 +513,7 @@ __global__ void __launch_bounds__(B) step_kernel(StepArgs<double> a) {
   Count cnt;
   size_t k = 0;
   int code = 0;
+  unsigned long long missing = 0;
   if (active) {
     k = (size_t)y * pr.nx + x;
     code = a.nxt_in[k];
@@ -458,29 +526,68 @@ __global__ void __launch_bounds__(B) step_kernel(StepArgs<double> a) {
       if (!gh && a.lat_in[ks] == code) {
         col[i * B] = a.pop_in[i * ps + ks];
         col[(Q + i) * B] = a.pop_in[(Q + i) * ps + ks];
-      } else {
-        s_queue[atomicAdd(&s_count, 1)] = (unsigned short)((t << 6) | i);
+        continue;
       }
+      missing |= 1ull << i;
+      const unsigned key = rebuild_key(sx, sy, x0, y, code);
+      unsigned short pos = NOSLOT;
+      unsigned h = (key * 2654435761u) >> 23;  // 9 bits: HCAP = 512
+      for (int probe = 0; probe < HCAP; ++probe, h = (h + 1) & (HCAP - 1)) {
+        const unsigned old = atomicCAS(&s_hkey[h], EMPTY, key);
+        if (old == EMPTY) {
+          const int slot = atomicAdd(&s_nslots, 1);
+          s_hslot[h] = slot < SCAP ? (unsigned short)slot : NOSLOT;
+          if (slot < SCAP) s_skey[slot] = key;
+          pos = (unsigned short)h;
+          break;
+        }
+        if (old == key) {
+          pos = (unsigned short)h;
+          break;
+        }
+      }
+      s_pos[i * B + t] = pos;
     }
   }
   __syncthreads();
-  // missing pulls, round-robin over the block; each thread solves in its own
-  // equilibrium column and writes into the owner's population column
-  const int nq = s_count;
-  for (int e = t; e < nq; e += B) {
-    const int owner = s_queue[e] >> 6, i = s_queue[e] & 63;
-    const int ox = x0 + owner;
-    const int ocode = a.nxt_in[(size_t)y * pr.nx + ox];
-    const int Upx = lat_ux(ocode), Upy = lat_uy(ocode);
-    double fd, gd;
-    cnt.rec += 1;
-    cnt.rec_fail += rebuild(pr, a.mom_in, ps, i, Upx, Upy, ox - vx(i) - Upx, y - vy(i) - Upy,
-                            &fd, &gd, eq, s_tab, &cnt);
-    smem49[i * B + owner] = fd;
-    smem49[(Q + i) * B + owner] = gd;
+  // phase 2: one solve per distinct (sender, lattice), round-robin
+  const int ns = s_nslots < SCAP ? s_nslots : SCAP;
+  for (int e = t; e < ns; e += B) {
+    const unsigned key = s_skey[e];
+    const int c = (int)(key % 49u), off = (int)(key / 49u);
+    const int sx = x0 + off % KW - 6, sy = y + off / KW - 6;
+    const Sender snd = sender_state(pr, a.mom_in, ps, sx, sy);
+    double lam[M];
+    const int st = sender_solve(pr, snd, lat_ux(c), lat_uy(c), eq, s_tab, lam, &cnt);
+    s_sok[e] = st == NEWTON_OK ? 1 : 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) s_lam[e * M + j] = lam[j];
   }
   __syncthreads();
   if (active) {
+    // phase 3: the node's missing pulls from the solves, then its collision
+    const int Upx = lat_ux(code), Upy = lat_uy(code);
+    for (int i = 0; i < Q; ++i) {
+      if (!((missing >> i) & 1ull)) continue;
+      const int sx = x - vx(i) - Upx, sy = y - vy(i) - Upy;
+      const unsigned short pos = s_pos[i * B + t];
+      const unsigned short slot = pos == NOSLOT ? NOSLOT : s_hslot[pos];
+      double fd, gd;
+      cnt.rec += 1;
+      if (slot == NOSLOT) {
+        cnt.rec_fail += rebuild(pr, a.mom_in, ps, i, Upx, Upy, sx, sy, &fd, &gd, eq, s_tab, &cnt);
+      } else {
+        const Sender snd = sender_state(pr, a.mom_in, ps, sx, sy);
+        if (s_sok[slot]) {
+          grad_value(pr, snd, i, Upx, Upy, s_lam + slot * M, s_tab, &fd, &gd);
+        } else {
+          fallback_value(pr, snd, i, Upx, Upy, &fd, &gd);
+          cnt.rec_fail += 1;
+        }
+      }
+      col[i * B] = fd;
+      col[(Q + i) * B] = gd;
+    }
     uint8_t nb[8];
     if (pr.overlap > 0.0 && pr.rule == 1) neighbours(pr, a.nxt_in, x, y, nb);
     collide(pr, col, eq, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, nb, s_tab,
