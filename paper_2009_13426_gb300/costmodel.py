@@ -174,16 +174,17 @@ if __name__ == "__main__":
 # pivots (690), two triangular solves (182), one line-search evaluation of
 # the 49 exponentials with the dual value (1060); per solve, targets, the
 # Maxwellian start's evaluation, log and normalisation (1220); per node,
-# moments, shift choice and BGK store (550); per rebuilt pull, gradients and
-# Grad factors (70).
+# moments, shift choice and BGK store (550); per rebuilt pull, the sender's
+# central differences, its exponential from the shared solve's multipliers
+# and the Grad factors (107).
 Q49_PER_ITER = 664 + 45 + 140 + 690 + 182 + 13 + 1060
 Q49_PER_CALL = 1220
 Q49_PER_NODE = 550
-Q49_PER_REBUILD = 70
-# ncu counted 45,952 FP64-pipe thread instructions per node on the 512^2
-# shear layer (11.46 Newton steps, 2.32 solves, 1.32 rebuilds per node),
-# where the count above gives 35,548.
-CALIBRATION["q49"] = 45952.0 / 35548.0
+Q49_PER_REBUILD = 12 + 9 + 9 + 1 + 40 + 3 * W_DIV + 8
+# ncu counted 30,696 FP64-pipe thread instructions per node on the 512^2
+# shear layer (7.10 Newton steps, 1.26 solves, 1.32 rebuilt pulls per node),
+# where the count above gives 22,067.
+CALIBRATION["q49"] = 30696.0 / 22067.0
 
 
 def q49_slots(delta, node_updates):
