@@ -3,14 +3,17 @@
 Workload (one GPU): 4096 x 4096 periodic double shear layer, streams at
 +-Mach 2.5 of the cold stream (T_cold = 0.35, temperature ratio 3, tanh width 8),
 seeded transverse perturbations in modes 1..8, nu = 1e-5, gamma = 1.4, shifts
-in {-2..2}^2, FP32 populations with FP64 Newton. A bench step is one time
-step of the whole flow (one launch of the fused step kernel). The state is
-5.7 GB (FP32 form), far larger than L2, so no flush is needed between steps.
+in {-2..2}^2, kinetic sensor on, FP32 populations with FP64 Newton. A bench
+step is one time step of the whole flow (one launch of the fused step
+kernel). The state is 5.7 GB (FP32 form), far larger than L2, so no flush is
+needed between steps. The headline times the steps after the warm-up from
+the initial state.
 
 Reported beside it: the FP64 plain path on the same flow (MLUPS and the FP32
-form's moment error against it), the end-to-end figure through the C ABI with
-host buffers, the FP64-pipe roofline of the step kernel, and the CPU oracle
-on a bounded sample of the same flow.
+form's moment error against it), the same FP32 flow once developed (steps
+1900-2000 of the workload's 2000), the end-to-end figure through the C ABI
+with host buffers, the FP64-pipe roofline of the step kernel, and the CPU
+oracle on a bounded sample of the same flow.
 
 Two sub-results run after it on one GPU (skipped under torchrun with N > 1):
 
@@ -58,6 +61,13 @@ METRIC = "adaptive D2Q21 MLUPS, FP32 form vs FP64 plain at stated error; serve p
 TRAFFIC_BYTES_PER_NODE_FP32 = 635.4
 UNIT = "MLUPS"
 NU = 1e-5
+# The kinetic sensor (Sec. IV.A.2) is on in every timed flow: without it the
+# nu = 1e-5 shear layer loses realizability after 300-400 steps in both
+# precisions (and in the FP64 oracle), and long serving requests fail.
+SENSOR = 1
+# step count of the shear-layer workload; its last 100 steps are timed as the
+# developed flow
+DEVELOPED_STEPS = 2000
 
 
 def parse():
@@ -69,6 +79,9 @@ def parse():
     ap.add_argument("--side", "--n", dest="n", type=int, default=4096,
                     help="grid side of the shear layer (--side under torchrun)")
     ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--developed-steps", type=int, default=DEVELOPED_STEPS,
+                    help="advance the FP32 flow to this step and time the last 100 "
+                         "(0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -187,7 +200,7 @@ def aggregate_mlups(world, nodes, steps, ms_max):
 
 def workload_config(n, world):
     return {"workload": "shear layer %dx%d periodic, Mach 2.5 cold stream, T ratio 3, "
-                        "nu 1e-5, FP32 populations, FP64 Newton" % (n, n),
+                        "nu 1e-5, kinetic sensor on, FP32 populations, FP64 Newton" % (n, n),
             "nodes": n * n, "u_max": 2, "l2_flush": "not needed: 5.7 GB state >> L2",
             "parallelism": "replica per GPU" if world > 1 else "single GPU"}
 
@@ -207,7 +220,8 @@ def oracle_sample(n, steps, warmup=1):
     total_time = 0.0
     for name, y0 in bands.items():
         band = [a[y0:y0 + rows].copy() for a in f]
-        s = O.Simulation(O.make_config(n, rows, umax=2, nu=NU, bc_y=O.ZERO_GRADIENT))
+        s = O.Simulation(O.make_config(n, rows, umax=2, nu=NU, bc_y=O.ZERO_GRADIENT,
+                                            sensor=bool(SENSOR)))
         assert s.init(*band) == O.OK
         if warmup:
             s.step(warmup)
@@ -266,7 +280,7 @@ def run_batched(args):
     specs = flows.batched_flows(256)[:args.batched_flows]
     nodes = sum(sp.nx * sp.ny for sp in specs)
     stream = torch.cuda.Stream()
-    b = alb.Batch([dict(nx=sp.nx, ny=sp.ny, nu=sp.nu, precision=alb.ALB_FP32_FORM)
+    b = alb.Batch([dict(nx=sp.nx, ny=sp.ny, nu=sp.nu, precision=alb.ALB_FP32_FORM, sensor=SENSOR)
                    for sp in specs], stream=stream)
     try:
         for sp, fl in zip(specs, b.flows):
@@ -348,7 +362,7 @@ def _serve_stream(alb, reqs, window, drain):
             prec = alb.ALB_FP32_FORM if sp.precision == "fp32" else alb.ALB_FP64_PLAIN
             try:
                 rid = srv.submit(sp.steps, fill=fill_of(sp), keep_result=False, nx=sp.nx,
-                                 ny=sp.ny, nu=sp.nu, precision=prec)
+                                 ny=sp.ny, nu=sp.nu, precision=prec, sensor=SENSOR)
                 ids[rid] = sp
             except alb.AlbError:
                 rejected += 1
@@ -436,7 +450,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream()
 
     def make(precision):
-        fl = alb.Flow(n, n, u_max=2, nu=NU, precision=precision, stream=stream)
+        fl = alb.Flow(n, n, u_max=2, nu=NU, precision=precision, sensor=SENSOR, stream=stream)
         fl.init(*fields)
         return fl
 
@@ -515,6 +529,44 @@ def run_ours(args, world, rank, local):
                                     "FP32 round-off of a shift threshold may take another lattice, "
                                     "which changes it at O(1e-2))"}
         fl64.close()
+
+    # The same flow once developed: advanced (untimed) to step
+    # developed_steps - 100, then the last 100 steps timed. The vortices of the
+    # rolled-up layers need more FP32 Newton steps and refinements per node.
+    developed = None
+    k_dev = 100
+    if args.developed_steps >= total32 + k_dev:
+        clocks_d = ClockSampler(local)
+        adv = args.developed_steps - k_dev - total32
+        for _ in range(adv // 100):
+            alb.alb_step(fl32.h, 100)
+        ms_a, _ = timed(fl32, 0, adv % 100)
+        clocks_d.start()
+        ms_d, dd = timed(fl32, k_dev, 0)
+        clk_d = clocks_d.stop()
+        ms_d = dist_max(ms_d, world)
+        slots_d = costmodel.fp64_slots(dd, "fp32")
+        tf_d = 2.0 * slots_d / (ms_d * 1e-3) / 1e12
+        developed = {"value": round(aggregate_mlups(world, N, k_dev, ms_d), 2), "unit": UNIT,
+                     "steps": [args.developed_steps - k_dev, args.developed_steps],
+                     "ms_per_step": round(ms_d / k_dev, 3),
+                     "per_node": {k: round(dd[k] / (N * k_dev), 4)
+                                  for k in ("fp32_iterations", "fp64_evaluations",
+                                            "newton_calls", "reconstructions")},
+                     "failures": {"node": dd["newton_failures"],
+                                  "rebuild": dd["reconstruction_failures"]},
+                     "roofline": {"bound": "alu", "achieved": round(tf_d, 4),
+                                  "peak": round(costmodel.FP64_PEAK_TFLOPS, 4),
+                                  "unit": "TFLOP/s",
+                                  "frac": round(tf_d / costmodel.FP64_PEAK_TFLOPS, 4),
+                                  "note": "FP64 slots only: the FP32 Newton steps, more "
+                                          "than two per node here, are not counted"},
+                     "clocks": clk_d}
+        r, a, b, e = fl32.moments()
+        T = (e / r - 0.5 * ((a / r) ** 2 + (b / r) ** 2)) / 2.5
+        developed["state"] = {"finite": bool(np.isfinite(r).all() and np.isfinite(e).all()),
+                              "rho_min": float("%.4g" % r.min()),
+                              "T_min": float("%.4g" % T.min())}
     st = fl32.stats()
     fl32.close()
 
@@ -529,7 +581,7 @@ def run_ours(args, world, rank, local):
         for name, rule in (("history", alb.ALB_RULE_HISTORY),
                            ("neighbourhood", alb.ALB_RULE_NEIGHBOURS)):
             flo = alb.Flow(n, n, u_max=2, nu=NU, precision=alb.ALB_FP32_FORM, stream=stream,
-                           shift_overlap=0.5, shift_rule=rule)
+                           shift_overlap=0.5, shift_rule=rule, sensor=SENSOR)
             flo.init(*fields)
             mso, dso = timed(flo, args.steps, args.warmup)
             ovl[name] = {"value": round(N * args.steps / (mso * 1e-3) / 1e6, 2),
@@ -545,7 +597,7 @@ def run_ours(args, world, rank, local):
         n49 = args.d2q49_side
         f49 = fields if n49 == n else flows.shear_layer(n49)
         fl = alb.Flow(n49, n49, stencil=alb.ALB_D2Q49, moments=13, u_max=2, nu=NU,
-                      precision=alb.ALB_FP64_PLAIN, stream=stream)
+                      precision=alb.ALB_FP64_PLAIN, sensor=SENSOR, stream=stream)
         fl.init(*f49)
         k49 = max(2, args.steps // 4)
         ms49, d49 = timed(fl, k49, min(args.warmup, 2))
@@ -571,21 +623,29 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         pinned = [torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).pin_memory() for a in fields]
         outs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(4)]
-        fl = alb.Flow(n, n, u_max=2, nu=NU, precision=alb.ALB_FP32_FORM, stream=stream)
+        fl = alb.Flow(n, n, u_max=2, nu=NU, precision=alb.ALB_FP32_FORM, sensor=SENSOR,
+                      stream=stream)
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         alb.alb_init(fl.h, *[p.numpy() for p in pinned])
-        alb.alb_step(fl.h, args.steps)
+        drift = None
+        for _ in range(args.steps):
+            alb.alb_step(fl.h, 1)
+            tot = alb.alb_totals(fl.h)  # the step's conservation totals, read to the host
+            drift = tot if drift is None else drift
         alb.alb_moments(fl.h, [o.numpy() for o in outs])
         dt = time.perf_counter() - t0
         dt = dist_max(dt, world)
+        mass_drift = abs(tot[0] - drift[0]) / abs(drift[0])
         fl.close()
         e2e = {"value": round(world * N * args.steps / dt / 1e6, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(4 * N * 8 / args.steps),
-               "d2h_bytes_per_step": int(4 * N * 8 / args.steps),
-               "note": "alb_init from pinned host fields + steps + alb_moments to pinned host, "
-                       "wall clock; bytes are the per-run copies divided by the steps"}
+               "d2h_bytes_per_step": int(4 * 8 + 4 * N * 8 / args.steps),
+               "note": "alb_init from pinned host fields, then every step alb_step and "
+                       "alb_totals (mass, momentum, energy read to the host), then alb_moments "
+                       "to pinned host; wall clock; the field copies are divided by the steps",
+               "mass_drift": float("%.3e" % mass_drift)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -626,6 +686,8 @@ def run_ours(args, world, rank, local):
                                         "newton_failures", "reconstruction_failures")},
     }
     line.update(extra)
+    if developed:
+        line["developed_flow"] = developed
     if ovl:
         line["overlapping_ranges"] = ovl
     if q49:
