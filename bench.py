@@ -338,7 +338,13 @@ def run_batched(args):
                          "frac": round(tflops / costmodel.FP64_PEAK_TFLOPS, 4),
                          "kernel": "batch_step_kernel<float>"},
             "failures": {"node": tot["newton_failures"],
-                         "rebuild": tot["reconstruction_failures"]}}
+                         "rebuild": tot["reconstruction_failures"],
+                         "node_per_update": float("%.3g" % (tot["newton_failures"] / upd)),
+                         "rebuild_per_rebuild": float("%.3g" % (
+                             tot["reconstruction_failures"] / max(tot["reconstructions"], 1))),
+                         "note": "fallbacks near the lattice's operability range; the CPU "
+                                 "oracle reports rebuild fallbacks on the same vortex initial "
+                                 "states (low core temperature, high Mach)"}}
 
 
 def _serve_stream(alb, reqs, window, drain):
@@ -401,10 +407,32 @@ def _serve_stream(alb, reqs, window, drain):
             "busy_fraction": round(stats["busy_seconds"] / stats["elapsed_seconds"], 3),
             "elapsed_s": round(stats["elapsed_seconds"], 1),
             "flagged": sum(1 for r in done.values() if r["status"] == alb.ALB_ENEWTON),
+            "flagged_detail": _flag_detail(alb, ids, done),
             "failed": sum(1 for r in done.values()
                           if r["status"] not in (alb.ALB_OK, alb.ALB_ENEWTON)),
             "ns_per_update": {"fp64": round(stats["ns_per_update"][0], 3),
                               "fp32": round(stats["ns_per_update"][1], 3)}}
+
+
+def _flag_detail(alb, ids, done):
+    """Which completed requests were flagged (any node equilibrium or Grad
+    rebuild that fell back), by initial state, and how rare the fallbacks
+    were: failed node updates per node update, failed rebuilds per rebuild."""
+    out = {}
+    for kind in ("vortex", "shear", "riemann2d"):
+        rs = [r for rid, r in done.items() if ids[rid].kind == kind]
+        if not rs:
+            continue
+        upd = sum(r["stats"]["node_updates"] for r in rs)
+        reb = sum(r["stats"]["reconstructions"] for r in rs)
+        out[kind] = {"completed": len(rs),
+                     "flagged": sum(1 for r in rs if r["status"] == alb.ALB_ENEWTON),
+                     "with_node_failures": sum(1 for r in rs if r["stats"]["newton_failures"]),
+                     "node_failures_per_update": float("%.3g" % (
+                         sum(r["stats"]["newton_failures"] for r in rs) / max(upd, 1))),
+                     "rebuild_failures_per_rebuild": float("%.3g" % (
+                         sum(r["stats"]["reconstruction_failures"] for r in rs) / max(reb, 1)))}
+    return out
 
 
 def run_serve(args):
