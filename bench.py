@@ -55,10 +55,10 @@ from paper_2009_13426_gb300 import costmodel, flows  # noqa: E402
 METRIC = "adaptive D2Q21 MLUPS, FP32 form vs FP64 plain at stated error; serve p50/p99"
 # DRAM bytes (read + write) per node update of step_kernel<float>, from one
 # ncu capture of the 1024^2 case of the same flow (dram__bytes_read.sum +
-# dram__bytes_write.sum = 666.3 MB per launch for 1,048,576 nodes, mean of 4
-# launches); the traffic grows in proportion to the nodes, so a 4096^2 launch
-# moves 16,777,216 x this. Measured on the current kernel.
-TRAFFIC_BYTES_PER_NODE_FP32 = 635.4
+# dram__bytes_write.sum = 710.6 MB per launch for 1,048,576 nodes, mean of 3
+# launches, kinetic sensor on); the traffic grows in proportion to the nodes,
+# so a 4096^2 launch moves 16,777,216 x this. Measured on the current kernel.
+TRAFFIC_BYTES_PER_NODE_FP32 = 677.7
 UNIT = "MLUPS"
 NU = 1e-5
 # The kinetic sensor (Sec. IV.A.2) is on in every timed flow: without it the
@@ -305,7 +305,7 @@ def run_batched(args):
         _sync_flagged(b, alb)
         s1 = [fl.stats() for fl in b.flows]
         tot = {key: sum(x[key] - y[key] for x, y in zip(s1, s0))
-               for key in ("fp64_evaluations", "fp32_iterations", "newton_calls",
+               for key in ("fp64_evaluations", "fp64_updates", "fp32_iterations", "newton_calls",
                            "newton_iterations", "reconstructions", "newton_failures",
                            "reconstruction_failures")}
         # the same flows one launch per flow and step (alb_step), same stream
@@ -579,7 +579,7 @@ def run_ours(args, world, rank, local):
                      "steps": [args.developed_steps - k_dev, args.developed_steps],
                      "ms_per_step": round(ms_d / k_dev, 3),
                      "per_node": {k: round(dd[k] / (N * k_dev), 4)
-                                  for k in ("fp32_iterations", "fp64_evaluations",
+                                  for k in ("fp32_iterations", "fp64_evaluations", "fp64_updates",
                                             "newton_calls", "reconstructions")},
                      "failures": {"node": dd["newton_failures"],
                                   "rebuild": dd["reconstruction_failures"]},
@@ -710,6 +710,7 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "gpu_launches": args.steps,
         "counters": {k: st[k] for k in ("newton_iterations", "newton_calls", "fp64_evaluations",
+                                        "fp64_updates",
                                         "fp32_iterations", "reconstructions",
                                         "newton_failures", "reconstruction_failures")},
     }

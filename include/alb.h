@@ -161,6 +161,10 @@ typedef struct {
   uint64_t newton_calls;            /* equilibrium solves, node and rebuild */
   uint64_t fp64_evaluations;        /* FP64 evaluations of the 21 exponentials */
   uint64_t fp32_iterations;         /* FP32 Newton steps (FP32 form) */
+  uint64_t fp64_updates;            /* FP32 form: residual evaluations that updated
+                                       the 21 FP64 populations multiplicatively
+                                       after a small step instead of evaluating
+                                       the exponentials (not in fp64_evaluations) */
 } alb_stats;
 
 /* Fill *cfg with defaults: 64x64, D2Q21, u_max 2, nu 1e-3, gamma 1.4,
@@ -275,7 +279,9 @@ const char* alb_last_error(void);
  * (full FP64 Newton if that fails). Writes feq[k*21 + i] (velocity order of
  * alb_velocities), lambda[k*8 + j] if lambda != NULL (order 0, x, y, xx, xy,
  * yy, x|xi|^2, y|xi|^2), iters[k] (FP64 Newton steps, or FP64 residual
- * evaluations for ALB_FP32_FORM) and status[k] (0 converged, 1 not
+ * evaluations, full and multiplicative, for ALB_FP32_FORM; the latter's
+ * populations are exponential-family members to about 1e-10 relative, their
+ * constraint residuals exact FP64 sums) and status[k] (0 converged, 1 not
  * converged, 2 singular / non-finite, 3 unrealizable input) if non-NULL. */
 int alb_equilibrium(const double* rho, const double* ubx, const double* uby, const double* T,
                     int n, double tol, int maxit, int precision, double* feq, double* lambda,

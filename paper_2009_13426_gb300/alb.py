@@ -66,7 +66,8 @@ class alb_config(ctypes.Structure):
 class alb_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "steps", "node_updates", "newton_iterations", "newton_failures", "reconstructions",
-        "reconstruction_failures", "newton_calls", "fp64_evaluations", "fp32_iterations")]
+        "reconstruction_failures", "newton_calls", "fp64_evaluations", "fp32_iterations",
+        "fp64_updates")]
 
 
 class alb_batch_tuning(ctypes.Structure):

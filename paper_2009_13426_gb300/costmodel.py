@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # step kernel to the slots this model gives for the same launch; it absorbs
 # what the hand count misses (compiler scheduling, predication) and is
 # measured again whenever a kernel changes.
-CALIBRATION = {"fp32": 1024.3 / 1122.5, "fp64": 5573.7 / 6073.3}
+CALIBRATION = {"fp32": 767.2 / 853.3, "fp64": 5573.7 / 6073.3}
 
 BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
                   "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}
@@ -111,6 +111,14 @@ def mixed_eval():
     return 55 + 21 * 7 + 68 + 17 + 24
 
 
+def mixed_update():
+    """Multiplicative FP64 update of the refinement after a small step: per
+    velocity the FP32 factor exp(-d) - 1 converted to FP64 and one FMA
+    (21 x 2; the exponent changes d are FP32), grouped constraint sums (68),
+    residual and its maximum (17), conversions and the update (24)."""
+    return 21 * 2 + 68 + 17 + 24
+
+
 def mixed_call():
     """Targets and conversions of the inputs and the FP32 multipliers."""
     return 8 + 8 + 3
@@ -136,6 +144,7 @@ def fp64_slots(stats: dict, precision: str) -> float:
     """FP64 slots of the work recorded by the kernel counters (a stats delta)."""
     if precision == "fp32":
         raw = (stats["fp64_evaluations"] * mixed_eval()
+               + stats.get("fp64_updates", 0) * mixed_update()
                + stats["newton_calls"] * mixed_call())
         # full FP64 Newton fallback, if any: its steps and evaluations
         raw += stats["newton_iterations"] * (plain_newton_step() + plain_eval() - mixed_eval())
@@ -154,6 +163,7 @@ def describe():
         "plain_newton_step": round(plain_newton_step(), 1),
         "plain_call": round(plain_call(), 1),
         "mixed_eval": round(mixed_eval(), 1),
+        "mixed_update": round(mixed_update(), 1),
         "mixed_call": round(mixed_call(), 1),
         "collision": {k: round(v, 1) for k, v in COLLISION.items()},
         "rebuild_extra": {k: round(v, 1) for k, v in REBUILD_EXTRA.items()},

@@ -574,6 +574,7 @@ int alb_stats_get(alb_handle* h, alb_stats* out) {
   out->newton_calls = h->ctr_host[CTR_NEWTON_CALLS];
   out->fp64_evaluations = h->ctr_host[CTR_FP64_EVALS];
   out->fp32_iterations = h->ctr_host[CTR_FP32_ITERS];
+  out->fp64_updates = h->ctr_host[CTR_FP64_UPDATES];
   return ALB_OK;
 }
 

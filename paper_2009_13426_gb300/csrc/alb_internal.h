@@ -20,7 +20,8 @@ enum Counter {
   CTR_NEWTON_CALLS = 5,   // equilibrium solves (node + rebuild)
   CTR_FP64_EVALS = 6,     // FP64 evaluations of the 21 exponentials
   CTR_FP32_ITERS = 7,     // FP32 Newton steps
-  CTR_COUNT = 8
+  CTR_FP64_UPDATES = 8,   // multiplicative FP64 updates of the 21 populations
+  CTR_COUNT = 9
 };
 
 // Device state of one flow: double-buffered population, lattice and moment

@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(BLOCK)
   if (lambda)
 #pragma unroll
     for (int j = 0; j < NM; ++j) lambda[(size_t)k * NM + j] = lam[j];
-  if (iters) iters[k] = precision == 0 ? (int)cnt.fp64_iters : (int)cnt.fp64_evals;
+  if (iters)
+    iters[k] = precision == 0 ? (int)cnt.fp64_iters : (int)(cnt.fp64_evals + cnt.fp64_updates);
   if (status) status[k] = st;
 }
 

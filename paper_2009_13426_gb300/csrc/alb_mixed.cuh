@@ -30,10 +30,12 @@ namespace alb {
 
 // Calls v.rest(s_0), v.pair<a, axis, i+, i->(s_+, s_-) and
 // v.quad<a, i++, i-+, i--, i+->(...) with the exponents
-// s_i = 1 + lambda . P(xi_i) of every group (index order of XI_X / XI_Y).
+// s_i = base + lambda . P(xi_i) of every group (index order of XI_X / XI_Y);
+// base is 1 for the exponents of Eq. exponential, 0 for the change of the
+// exponents under a step of the multipliers.
 template <typename R, typename V>
-__device__ __forceinline__ void visit_groups(const R l[NM], V& v) {
-  const R c = (R)1 + l[0];
+__device__ __forceinline__ void visit_groups(const R l[NM], V& v, R base = (R)1) {
+  const R c = base + l[0];
   v.rest(c);
   {  // axis, |xi| = 1
     const R ex = c + l[3], ox = l[1] + l[6];
@@ -175,6 +177,46 @@ struct PassGH32 {
   }
 };
 
+// FP64 constraint sums M = sum p P over the groups of the velocity set, the
+// grouping of PassG64: a symmetric pair enters through its sum and
+// difference, a diagonal quadruple through its four parity combinations.
+struct SumsG64 {
+  double M[NM];
+  __device__ __forceinline__ SumsG64() {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) M[k] = 0.0;
+  }
+  __device__ __forceinline__ void add_rest(double p) { M[0] += p; }
+  template <int A, int AX>
+  __device__ __forceinline__ void add_pair(double pp, double pm) {
+    const double S = pp + pm, D = pp - pm;
+    M[0] += S;
+    if (AX == 0) {
+      M[1] = madd(M[1], D, A);
+      M[3] = madd(M[3], S, A * A);
+      M[6] = madd(M[6], D, A * A * A);
+    } else {
+      M[2] = madd(M[2], D, A);
+      M[5] = madd(M[5], S, A * A);
+      M[7] = madd(M[7], D, A * A * A);
+    }
+  }
+  template <int A>
+  __device__ __forceinline__ void add_quad(double ppp, double pmp, double pmm, double ppm) {
+    const double Ap = ppp + ppm, Bm = pmp + pmm;  // sx = +1, sx = -1
+    const double Cp = ppp - ppm, Dm = pmp - pmm;
+    const double sum = Ap + Bm, xs = Ap - Bm, ys = Cp + Dm, xys = Cp - Dm;
+    M[0] += sum;
+    M[1] = madd(M[1], xs, A);
+    M[2] = madd(M[2], ys, A);
+    M[3] = madd(M[3], sum, A * A);
+    M[4] = madd(M[4], xys, A * A);
+    M[5] = madd(M[5], sum, A * A);
+    M[6] = madd(M[6], xs, 2 * A * A * A);
+    M[7] = madd(M[7], ys, 2 * A * A * A);
+  }
+};
+
 // FP64 pass: the constraint sums M = sum p P with p = exp(-s) in FP64, each p
 // also written to the caller's shared column (p_i at col[i * stride]);
 // REFINE selects the cheaper exponential of the FP32 form's refinement.
@@ -232,6 +274,38 @@ struct PassG64 {
     M[5] = madd(M[5], sum, A * A);
     M[6] = madd(M[6], xs, 2 * A * A * A);
     M[7] = madd(M[7], ys, 2 * A * A * A);
+  }
+};
+
+// Multiplicative pass of the FP32 form's refinement: after a step dl of the
+// multipliers, p_i(lambda + dl) = p_i(lambda) exp(-d_i) with d_i = dl . P(xi_i)
+// (Eq. exponential), so the populations in the column are updated in place,
+// p_i <- p_i + p_i (exp(-d_i) - 1), and the FP64 sums taken again. d_i and
+// exp(-d_i) - 1 = -d (1 - d/2 + d^2/6) are formed in FP32 (the step is an FP32
+// vector); for |d_i| <= 1e-3 (checked by the caller) the update's factor has
+// a relative error of about 1e-10, so the column stays an exponential-family
+// member to that level, while the sums that decide convergence are exact FP64
+// sums of the column. Two FP64 operations per velocity instead of an
+// exponent and an exponential.
+struct PassMul64 : SumsG64 {
+  double* col;
+  int stride;
+  __device__ __forceinline__ PassMul64(double* c, int s) : col(c), stride(s) {}
+  __device__ __forceinline__ double upd(int i, float d) const {
+    const float e = d * fmaf(d, fmaf(d, -1.0f / 6.0f, 0.5f), -1.0f);
+    double* q = col + (size_t)i * stride;
+    const double p = fma(*q, (double)e, *q);
+    *q = p;
+    return p;
+  }
+  __device__ __forceinline__ void rest(float d) { add_rest(upd(0, d)); }
+  template <int A, int AX, int IP, int IM>
+  __device__ __forceinline__ void pair(float dp, float dm) {
+    add_pair<A, AX>(upd(IP, dp), upd(IM, dm));
+  }
+  template <int A, int IPP, int IMP, int IMM, int IPM>
+  __device__ __forceinline__ void quad(float dpp, float dmp, float dmm, float dpm) {
+    add_quad<A>(upd(IPP, dpp), upd(IMP, dmp), upd(IMM, dmm), upd(IPM, dpm));
   }
 };
 
@@ -411,35 +485,70 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
   return NEWTON_OK;
 }
 
+// max_i |P_k(xi_i)| over the velocity set (compile time).
+__host__ __device__ constexpr int pm_max(int k) {
+  int m = 0;
+  for (int i = 0; i < Q; ++i) m = PM(k, i) > m ? PM(k, i) : (-PM(k, i) > m ? -PM(k, i) : m);
+  return m;
+}
+
+// Largest |dl . P(xi_i)| over the velocities is at most this bound (FP32);
+// the weights are max_i |P_k(xi_i)|, checked at compile time.
+static_assert(pm_max(0) == 1 && pm_max(1) == 3 && pm_max(2) == 3 && pm_max(3) == 9 &&
+                  pm_max(4) == 4 && pm_max(5) == 9 && pm_max(6) == 27 && pm_max(7) == 27,
+              "monomial bounds of the D2Q21 set");
+__device__ __forceinline__ float step_exponent_bound(const float dl[NM]) {
+  return fabsf(dl[0]) + 3.0f * (fabsf(dl[1]) + fabsf(dl[2])) + 4.0f * fabsf(dl[4]) +
+         9.0f * (fabsf(dl[3]) + fabsf(dl[5])) + 27.0f * (fabsf(dl[6]) + fabsf(dl[7]));
+}
+
 // FP64 refinement: lambda <- lambda + H32^-1 G64(lambda) until max|G|/rho <= tol.
+// The first residual evaluates the 21 exponentials in FP64; after a step whose
+// exponent changes are all below 1e-3 in magnitude, the next one updates the
+// column multiplicatively instead (PassMul64), else it evaluates them again.
 // On NEWTON_OK the FP64 equilibrium per unit density at the returned lambda
 // is in col[i * stride] (a shared-memory column of the calling thread).
+// *evals counts the full evaluations, *updates the multiplicative ones.
 static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T, double tol,
                                                int maxr, const float lam32[NM], const Fact32& fc,
                                                const double* tab, double* col, int stride,
-                                               double lam[NM], int* evals) {
+                                               double lam[NM], int* evals, int* updates) {
   double m[NM];
   targets(ubx, uby, T, m);
 #pragma unroll
   for (int k = 0; k < NM; ++k) lam[k] = (double)lam32[k];
   *evals = 0;
+  *updates = 0;
+  float dl[NM];
+  bool small_step = false;
   for (int r = 0;; ++r) {
-    PassG64<true> ps(tab, col, stride);
-    visit_groups<double>(lam, ps);
-    ++*evals;
+    double M[NM];
+    if (small_step) {
+      PassMul64 pu(col, stride);
+      visit_groups<float>(dl, pu, 0.0f);
+      ++*updates;
+#pragma unroll
+      for (int k = 0; k < NM; ++k) M[k] = pu.M[k];
+    } else {
+      PassG64<true> ps(tab, col, stride);
+      visit_groups<double>(lam, ps);
+      ++*evals;
+#pragma unroll
+      for (int k = 0; k < NM; ++k) M[k] = ps.M[k];
+    }
     double gmax = 0.0;
     float g32[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
-      const double G = ps.M[k] - m[k];
+      const double G = M[k] - m[k];
       gmax = fmax(gmax, fabs(G));
       g32[k] = (float)G;
     }
     if (!isfinite(gmax)) return NEWTON_SINGULAR;
     if (gmax <= tol) return NEWTON_OK;
     if (r >= maxr) return NEWTON_MAXIT;
-    float dl[NM];
     solve32(fc, g32, dl);
+    small_step = step_exponent_bound(dl) <= 1e-3f;
 #pragma unroll
     for (int k = 0; k < NM; ++k) lam[k] += (double)dl[k];
   }
@@ -447,7 +556,7 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
 
 // Work counts of one equilibrium solve.
 struct SolveCount {
-  unsigned fp32_iters = 0, fp64_evals = 0, fp64_iters = 0;
+  unsigned fp32_iters = 0, fp64_evals = 0, fp64_iters = 0, fp64_updates = 0;
 };
 
 // Jacobian H = sum_i p_i P(xi_i) P(xi_i)^T (packed lower triangle) from the
@@ -816,8 +925,10 @@ __device__ __forceinline__ int equilibrium_mixed(double ubx, double uby, double 
     cnt->fp32_iters += it32;
   }
   if (st == NEWTON_OK) {
-    st = refine_fp64(ubx, uby, T, tol, 6, lam32, fc, tab, col, stride, lam, &ev);
+    int up = 0;
+    st = refine_fp64(ubx, uby, T, tol, 6, lam32, fc, tab, col, stride, lam, &ev, &up);
     cnt->fp64_evals += ev;
+    cnt->fp64_updates += up;
   }
   if (st != NEWTON_OK) {
     int it = 0;

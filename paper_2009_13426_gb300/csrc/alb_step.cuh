@@ -364,6 +364,7 @@ __device__ __forceinline__ void flush_counts(unsigned long long* ctr, const Node
   warp_count(ctr + CTR_NEWTON_ITERS, c.solve.fp64_iters);
   warp_count(ctr + CTR_FP64_EVALS, c.solve.fp64_evals);
   warp_count(ctr + CTR_FP32_ITERS, c.solve.fp32_iters);
+  warp_count(ctr + CTR_FP64_UPDATES, c.solve.fp64_updates);
   warp_count(ctr + CTR_NEWTON_CALLS, c.calls);
   warp_count(ctr + CTR_NEWTON_FAIL, c.fail);
   warp_count(ctr + CTR_REC, c.rec);
