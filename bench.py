@@ -24,8 +24,9 @@ Two sub-results run after it on one GPU (skipped under torchrun with N > 1):
   MLUPS over all flows, beside the same flows stepped one launch per flow.
 * "serve": the serving loop under a Poisson stream of requests (50 per
   second for 60 s; sides 64-2048, 100-5000 steps, FP32 or FP64 form, vortex,
-  shear-layer or 2D-Riemann initial data): completion latency p50/p99,
-  served versus offered node updates; then a stream of the same shape on a
+  shear-layer or 2D-Riemann initial data, the last with zero-gradient
+  ends): completion latency p50/p99, served versus offered node updates;
+  flagged requests by initial state; then a stream of the same shape on a
   reduced range (sides 64-512, 100-1000 steps) at about 70 % of the
   measured capacity, drained to completion (bounded).
 
@@ -366,9 +367,13 @@ def _serve_stream(alb, reqs, window, drain):
             while time.perf_counter() - t0 < sp.arrival:
                 time.sleep(0.0005)
             prec = alb.ALB_FP32_FORM if sp.precision == "fp32" else alb.ALB_FP64_PLAIN
+            # the 2D Riemann problem with the paper's zero-gradient ends: periodic
+            # ends would add the reversed quadrant jumps at the box's edges
+            bc = alb.ALB_ZERO_GRADIENT if sp.kind == "riemann2d" else alb.ALB_PERIODIC
             try:
                 rid = srv.submit(sp.steps, fill=fill_of(sp), keep_result=False, nx=sp.nx,
-                                 ny=sp.ny, nu=sp.nu, precision=prec, sensor=SENSOR)
+                                 ny=sp.ny, nu=sp.nu, precision=prec, sensor=SENSOR, bc_x=bc,
+                                 bc_y=bc)
                 ids[rid] = sp
             except alb.AlbError:
                 rejected += 1
