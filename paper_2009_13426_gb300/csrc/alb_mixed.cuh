@@ -449,10 +449,18 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
       // The predicted decrease gd/2 of the dual lies below its FP32 resolution:
       // a line search would only compare rounding noise. This close to the root
       // the full Newton step is safe; take it and leave the rest to the FP64
-      // refinement (the factor of the previous multipliers serves it).
+      // refinement. The refinement contracts by about |I - H32^-1 H| per
+      // residual, so it gets the factor of the Jacobian at the new multipliers
+      // (one more FP32 pass): a factor one step old costs about one more FP64
+      // residual per solve.
 #pragma unroll
       for (int k = 0; k < NM; ++k) lam[k] += dl[k];
       ++it;
+      PassGH32 pn;
+      visit_groups<float>(lam, pn);
+      float Gn[NM];
+      pn.assemble(Gn, H);
+      if (!(isfinite(pn.F()) && factor32(H, fc))) return NEWTON_SINGULAR;
       break;
     }
     float t = 1.0f, lc[NM];

@@ -2,7 +2,9 @@
 
 * alb_equilibrium with ALB_FP32_FORM (FP32 Newton refined with FP64
   residuals) against the CPU oracle on 10^4 states: 1e-10 relative, the same
-  convergence decision, and few FP64 evaluations per state.
+  convergence decision, and few FP64 evaluations per state; after the
+  refinement's multiplicative updates the populations are still the
+  exponential of the returned multipliers to 1e-9.
 * alb_exp_neg (table-driven FP64 exponential, Tang's method) against CUDA's
   own exp: a few ulp.
 """
@@ -129,3 +131,47 @@ def test_refinement_exponential_within_its_bound(alb):
     torch.cuda.synchronize()
     o = o.cpu().numpy()
     assert o[0] == 0.0 and np.isinf(o[1])
+
+
+def test_refinement_keeps_the_exponential_form(alb):
+    """The FP32 form's refinement updates the FP64 populations in place after
+    small steps (p_i <- p_i exp(-dl . P(xi_i)), the factor in FP32): the
+    returned populations stay exp(-(1 + lambda . P(xi_i))) of the returned
+    multipliers (Eq. exponential) to 1e-9 relative, and a flow's step
+    performs such updates, counted apart from the full evaluations."""
+    from paper_2009_13426_gb300 import flows
+    rng = np.random.default_rng(41)
+    n = 4000
+    rho = rng.uniform(0.1, 3.0, n)
+    ang = rng.uniform(0, 2 * np.pi, n)
+    mag = rng.uniform(0, 1.4, n)
+    T = rng.uniform(0.3, 1.4, n)
+    ubx, uby = mag * np.cos(ang), mag * np.sin(ang)
+    feq = torch.empty(n * 21, dtype=torch.float64, device="cuda")
+    lam = torch.empty(n * 8, dtype=torch.float64, device="cuda")
+    its = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    alb.alb_equilibrium(_dev(rho), _dev(ubx), _dev(uby), _dev(T), n, 1e-12, 50, feq, lam, its,
+                        st, precision=alb.ALB_FP32_FORM)
+    torch.cuda.synchronize()
+    feq = feq.cpu().numpy().reshape(n, 21)
+    lam = lam.cpu().numpy().reshape(n, 8)
+    ok = st.cpu().numpy() == 0
+    assert ok.mean() > 0.95
+    x, y = O.velocities()
+    x = x.astype(float)
+    y = y.astype(float)
+    r2 = x * x + y * y
+    P = np.stack([np.ones(21), x, y, x * x, x * y, y * y, x * r2, y * r2])
+    pe = np.exp(-(1.0 + lam[ok] @ P))
+    rel = np.abs(feq[ok] / rho[ok, None] - pe) / pe
+    assert rel.max() <= 1e-9, rel.max()
+
+    fl = alb.Flow(64, 64, precision=alb.ALB_FP32_FORM, nu=1e-3)
+    fl.init(*flows.isentropic_vortex(64, 64, mach=1.2, seed=1))
+    fl.step(5)
+    fl.sync()
+    s = fl.stats()
+    assert s["fp64_updates"] > 0
+    assert s["fp64_evaluations"] <= 1.5 * s["newton_calls"]
+    fl.close()
