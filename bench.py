@@ -56,10 +56,10 @@ from paper_2009_13426_gb300 import costmodel, flows  # noqa: E402
 METRIC = "adaptive D2Q21 MLUPS, FP32 form vs FP64 plain at stated error; serve p50/p99"
 # DRAM bytes (read + write) per node update of step_kernel<float>, from one
 # ncu capture of the 1024^2 case of the same flow (dram__bytes_read.sum +
-# dram__bytes_write.sum = 710.6 MB per launch for 1,048,576 nodes, mean of 3
+# dram__bytes_write.sum = 713.5 MB per launch for 1,048,576 nodes, mean of 3
 # launches, kinetic sensor on); the traffic grows in proportion to the nodes,
 # so a 4096^2 launch moves 16,777,216 x this. Measured on the current kernel.
-TRAFFIC_BYTES_PER_NODE_FP32 = 677.7
+TRAFFIC_BYTES_PER_NODE_FP32 = 680.4
 UNIT = "MLUPS"
 NU = 1e-5
 # The kinetic sensor (Sec. IV.A.2) is on in every timed flow: without it the
