@@ -1,0 +1,48 @@
+"""The work model behind the benchmark's roofline (CPU only): the unit costs
+are consistent with the kernel's structure, and the slots follow the device
+counters, including the FP32 form's multiplicative updates."""
+import pytest
+
+from paper_2009_13426_gb300 import costmodel as C
+
+
+def base_stats(**kw):
+    st = {"newton_iterations": 0, "newton_calls": 100, "fp64_evaluations": 100,
+          "fp64_updates": 0, "fp32_iterations": 80, "reconstructions": 5, "node_updates": 100}
+    st.update(kw)
+    return st
+
+
+def test_update_is_cheaper_than_an_evaluation():
+    # an update replaces the 21 exponents and exponentials by a conversion and
+    # an FMA per velocity; the sums, residual and bookkeeping are shared
+    shared = 68 + 17 + 24
+    assert C.mixed_eval() - shared == 55 + 21 * 7
+    assert C.mixed_update() - shared == 21 * 2
+    assert C.mixed_update() < C.mixed_eval()
+
+
+def test_slots_follow_the_counters():
+    s0 = C.fp64_slots(base_stats(), "fp32")
+    s1 = C.fp64_slots(base_stats(fp64_updates=50), "fp32")
+    assert s1 - s0 == pytest.approx(50 * C.mixed_update() * C.CALIBRATION["fp32"])
+    s2 = C.fp64_slots(base_stats(fp64_evaluations=150), "fp32")
+    assert s2 - s0 == pytest.approx(50 * C.mixed_eval() * C.CALIBRATION["fp32"])
+
+
+def test_counters_without_updates_are_accepted():
+    st = base_stats()
+    del st["fp64_updates"]
+    assert C.fp64_slots(st, "fp32") == C.fp64_slots(base_stats(), "fp32")
+
+
+def test_calibrations_are_near_the_hand_count():
+    # ncu's FP64-pipe instruction count against the model's slots for the
+    # same launches: the hand count may miss a little, not a factor
+    for k in ("fp32", "fp64"):
+        assert 0.8 < C.CALIBRATION[k] < 1.1, k
+    assert 1.0 < C.CALIBRATION["q49"] < 1.6
+
+
+def test_peak_is_the_fp64_unit_count():
+    assert C.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
