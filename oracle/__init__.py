@@ -50,10 +50,15 @@ _bp = np.ctypeslib.ndpointer(dtype=np.int8, flags="C_CONTIGUOUS")
 _lib = None
 
 
+# A build of the oracle other than oracle/liboracle.so (used by the tests that
+# plant a mistake in a copy of the source and check that a pin catches it).
+OVERRIDE_ENV = "ALB_ORACLE_LIB_OVERRIDE"
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(_build.build())
+        L = ctypes.CDLL(os.environ.get(OVERRIDE_ENV) or _build.build())
         L.ora_velocities.argtypes = [ctypes.c_int, np.ctypeslib.ndpointer(np.int32),
                                      np.ctypeslib.ndpointer(np.int32)]
         L.ora_equilibrium13.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp,

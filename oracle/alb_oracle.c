@@ -819,12 +819,16 @@ int ora_init(ora_state* s, const double* rho, const double* rhoux, const double*
   return status;
 }
 
-/* Post-collision population of velocity i pulled by a node in lattice (Upx, Upy)
- * from the (possibly ghost) sender (sx, sy) whose lattice differs: Grad rebuild
- * with the sender's moments and gradients and the sender's relaxation time. */
-static int rebuild_pull(ora_state* s, int i, int Upx, int Upy, int sx, int sy, double* fi,
+/* Post-collision population of velocity i pulled by the receiver (x, y) in
+ * lattice (Upx, Upy) from the (possibly ghost) sender (sx, sy) = (x, y) -
+ * (xi_i + U') whose lattice differs: Grad rebuild with the sender's moments
+ * and gradients and the sender's relaxation time (Sec. III.B.2: the rebuilt
+ * population is the sender's post-collision one). */
+static int rebuild_pull(ora_state* s, int i, int Upx, int Upy, int x, int y, double* fi,
                         double* gi) {
   const ora_config* c = &s->cfg;
+  const int sx = x - (s->xi[i][0] + Upx);
+  const int sy = y - (s->xi[i][1] + Upy);
   int gx, gy;
   const int rx = resolve(sx, c->nx, c->bc_x, &gx);
   const int ry = resolve(sy, c->ny, c->bc_y, &gy);
@@ -946,7 +950,7 @@ static int step_once(ora_state* s, const signed char* forced_x, const signed cha
           gi = s->gs[(size_t)ks * Q + i];
         } else {
           rec += 1;
-          if (rebuild_pull(s, i, Upx, Upy, sx, sy, &fi, &gi) != ORA_OK) {
+          if (rebuild_pull(s, i, Upx, Upy, x, y, &fi, &gi) != ORA_OK) {
             rec_fail += 1;
             rebuild_fallback(s, i, Upx, Upy, sx, sy, &fi, &gi);
           }
