@@ -46,3 +46,13 @@ def test_calibrations_are_near_the_hand_count():
 
 def test_peak_is_the_fp64_unit_count():
     assert C.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+
+
+def test_method_floor_is_one_fp64_evaluation():
+    # one FP64 evaluation of the equilibrium without the residual bookkeeping:
+    # the least FP64 work a solve needs; at the FP64 peak it allows this rate
+    f = C.method_floor(500.0)
+    assert f["fp64_slots_per_node"] == C.mixed_eval() - 17 - 24
+    cap = 152 * 2 * 2.07e9 / f["fp64_slots_per_node"] / 1e6
+    assert f["mlups_at_fp64_peak"] == pytest.approx(cap, rel=1e-3)
+    assert f["frac"] == pytest.approx(500.0 / cap, rel=1e-3)

@@ -321,6 +321,11 @@ def test_sod_tube_matches_oracle(alb, precision, tol):
         assert (sx == rx).all() and (sy == ry).all()
     else:
         fl, s, differs = run_replay(alb, nx, ny, fields, steps, precision, **kw)
+        # lattice decisions that differ from the free-running FP64 oracle's
+        # (FP32 round-off at a threshold, then the runs part) stay rare
+        print("\nSod FP32 form: %d differing lattice decisions in %d node-steps"
+              % (differs, nx * ny * steps))
+        assert differs <= nx * ny * steps * 1e-4
     err = rel_errors(fl.moments(), s.moments())
     assert max(err.values()) <= tol, err
 

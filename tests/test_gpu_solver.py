@@ -84,6 +84,24 @@ def test_mixed_solver_reaches_the_criterion(alb):
         assert np.abs(P @ feq[k] - m).max() / rho[k] <= 1.5e-12
 
 
+# |s| past 2^31 ln2/256 (about 5.8e6) wraps the low word of the rounded
+# reduction index, and past 2^51 ln2/256 the rounding trick itself fails: the
+# result must still be 0 for large s and +inf for large -s.
+LIMITS = [1000.0, 5.9e6, 1e7, 3e9, 2.0 ** 40, 1e13, 1e16, 1e300]
+
+
+def _check_limits(fn):
+    s = np.array(LIMITS + [-v for v in LIMITS])
+    t = _dev(s)
+    o = torch.empty(s.size, dtype=torch.float64, device="cuda")
+    fn(t, s.size, o)
+    torch.cuda.synchronize()
+    o = o.cpu().numpy()
+    k = len(LIMITS)
+    assert (o[:k] == 0.0).all(), o[:k]
+    assert np.isinf(o[k:]).all() and (o[k:] > 0).all(), o[k:]
+
+
 def test_table_exponential_against_cuda_exp(alb):
     rng = np.random.default_rng(8)
     s = np.concatenate([rng.uniform(-30, 60, 400000), rng.uniform(-690, 690, 100000),
@@ -98,13 +116,7 @@ def test_table_exponential_against_cuda_exp(alb):
     ref = ref.cpu().numpy()
     rel = np.abs(got - ref) / ref
     assert rel.max() <= 4 * 2.0 ** -52, rel.max()
-    # limits: 0 far below, +inf far above the double range
-    t = _dev([1000.0, -1000.0])
-    o = torch.empty(2, dtype=torch.float64, device="cuda")
-    alb.alb_exp_neg(t, 2, o)
-    torch.cuda.synchronize()
-    o = o.cpu().numpy()
-    assert o[0] == 0.0 and np.isinf(o[1])
+    _check_limits(alb.alb_exp_neg)
 
 
 def test_refinement_exponential_within_its_bound(alb):
@@ -125,12 +137,7 @@ def test_refinement_exponential_within_its_bound(alb):
     rel = np.abs(out.cpu().numpy() - ref.cpu().numpy()) / ref.cpu().numpy()
     assert rel.max() <= 2e-13, rel.max()
     assert rel.max() > 4 * 2.0 ** -52  # it is the cheaper variant
-    t = _dev([1000.0, -1000.0])
-    o = torch.empty(2, dtype=torch.float64, device="cuda")
-    alb.alb_exp_neg_refine(t, 2, o)
-    torch.cuda.synchronize()
-    o = o.cpu().numpy()
-    assert o[0] == 0.0 and np.isinf(o[1])
+    _check_limits(alb.alb_exp_neg_refine)
 
 
 def test_refinement_keeps_the_exponential_form(alb):
