@@ -19,19 +19,38 @@
 
 namespace alb {
 
+// Launch shape of the step kernel per precision: the FP32 form runs blocks of
+// 256 threads, two per SM (measured on the 4096^2 shear layer once developed,
+// through the batch kernel's compiled shapes: 620 MLUPS against 591 for
+// 128 x 4 and 555 for 128 x 3); FP64 plain runs 128 threads with up to 255
+// registers each.
 template <typename P>
-__global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1))
-    step_kernel(StepArgs<P> a) {
+struct StepShape;
+template <>
+struct StepShape<float> {
+  static constexpr int B = 256, MINB = 2, LOG2B = 8;
+};
+template <>
+struct StepShape<double> {
+  static constexpr int B = 128, MINB = 1, LOG2B = 7;
+};
+
+// One time step of every node: block (bx, by) updates the tile of 2^lg nodes
+// along x by B >> lg rows at (bx << lg, by * (B >> lg)).
+template <typename P>
+__global__ void __launch_bounds__(StepShape<P>::B, StepShape<P>::MINB)
+    step_kernel(StepArgs<P> a, int lg) {
+  constexpr int B = StepShape<P>::B;
+  static_assert((1 << StepShape<P>::LOG2B) == B, "tiles of B nodes");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_tab[EXPT_N];
-  __shared__ RebuildQueue<BLOCK> s_rq;
+  __shared__ RebuildQueue<B> s_rq;
   if (threadIdx.x == 0) s_rq.count = 0;
   load_exptab(s_tab);  // includes a barrier
-  const Columns<P, BLOCK> cl(smem_raw);
-  constexpr int LG = BLOCK == 128 ? 7 : (BLOCK == 256 ? 8 : 6);
-  static_assert((1 << LG) == BLOCK, "row tiles of BLOCK nodes");
+  const Columns<P, B> cl(smem_raw);
   NodeCount nc;
-  tile_step<P, BLOCK>(a, blockIdx.x * BLOCK, blockIdx.y, LG, cl, s_tab, s_rq, nc);
+  tile_step<P, B>(a, blockIdx.x << lg, blockIdx.y << (StepShape<P>::LOG2B - lg), lg, cl, s_tab,
+                  s_rq, nc);
   flush_counts(a.ctr, nc);
 }
 
@@ -240,6 +259,18 @@ __global__ void select_kernel(const double* rho, const double* rhou, int n, doub
 
 static dim3 grid_of(const Params& p) { return dim3((p.nx + BLOCK - 1) / BLOCK, p.ny); }
 
+// Tiles of the step kernel: 2^lg nodes along x, the smallest power of two that
+// holds a row (at least 8, at most the block), and the block's other threads
+// on the following rows, so that narrow grids keep the threads busy.
+template <typename P>
+static dim3 step_grid(const Params& p, int* lg) {
+  int l = 3;
+  while (l < StepShape<P>::LOG2B && (1 << l) < p.nx) ++l;
+  *lg = l;
+  const int rows = StepShape<P>::B >> l;
+  return dim3((p.nx + (1 << l) - 1) >> l, (p.ny + rows - 1) / rows);
+}
+
 // Dynamic shared memory needs an explicit opt-in once static plus dynamic
 // shared memory exceed 48 KB; the dynamic size is always declared.
 template <typename K>
@@ -270,14 +301,19 @@ cudaError_t launch_step(FlowDev& f, cudaStream_t s) {
   if (f.q == 49) return launch_step_q49(f, s);
   const int in = f.cur, out = f.cur ^ 1;
   cudaError_t e;
+  int lg = 0;
   if (f.precision == 0) {
+    constexpr int B = StepShape<double>::B;
     const StepArgs<double> a = step_args<double>(f, in);
-    if ((e = allow_smem(step_kernel<double>, smem_bytes<double>())) != cudaSuccess) return e;
-    step_kernel<double><<<grid_of(f.prm), BLOCK, smem_bytes<double>(), s>>>(a);
+    const dim3 g = step_grid<double>(f.prm, &lg);
+    if ((e = allow_smem(step_kernel<double>, smem_bytes<double, B>())) != cudaSuccess) return e;
+    step_kernel<double><<<g, B, smem_bytes<double, B>(), s>>>(a, lg);
   } else {
+    constexpr int B = StepShape<float>::B;
     const StepArgs<float> a = step_args<float>(f, in);
-    if ((e = allow_smem(step_kernel<float>, smem_bytes<float>())) != cudaSuccess) return e;
-    step_kernel<float><<<grid_of(f.prm), BLOCK, smem_bytes<float>(), s>>>(a);
+    const dim3 g = step_grid<float>(f.prm, &lg);
+    if ((e = allow_smem(step_kernel<float>, smem_bytes<float, B>())) != cudaSuccess) return e;
+    step_kernel<float><<<g, B, smem_bytes<float, B>(), s>>>(a, lg);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) f.cur = out;

@@ -84,11 +84,27 @@ __device__ __forceinline__ void load_exptab(double* s_tab) {
   __syncthreads();
 }
 
+// Exponent e = n >> 8 of the scale 2^(n/N) of the table exponentials below.
+// t = 1.5 * 2^52 + n holds n exactly while |n| < 2^51, and its low word holds n
+// only while |n| < 2^31 (|s| below about 5.8e6); past that the low word wraps,
+// so e is saturated from the high word: 0x43380000 for 0 <= n < 2^32,
+// 0x4337ffff for -2^32 <= n < 0, larger or smaller beyond (also when the
+// rounding trick itself no longer applies). A non-finite t (s NaN or
+// infinite) keeps e in range, so that the NaN of the polynomial comes
+// through. Integer operations only.
+__device__ __forceinline__ int exp_scale_exponent(double t, int n) {
+  const int hi = __double2hiint(t);
+  const bool finite = (hi & 0x7ff00000) != 0x7ff00000;
+  const bool over = hi > 0x43380000 || (hi == 0x43380000 && n < 0);
+  const bool under = hi < 0x4337ffff || (hi == 0x4337ffff && n >= 0);
+  return !finite ? 0 : (over ? 4096 : (under ? -4096 : (n >> EXPT_BITS)));
+}
+
 // Table-driven FP64 exp(-s) (Tang's method with an N = 256 table): n nearest
 // to -s N / ln2, r = -s - n ln2/N in two parts (|r| <= ln2/512), exp(r) by its
 // degree-4 Taylor polynomial, times 2^(n/N) = 2^(n >> 8) tab[n & 255].
 // 9 FP64 operations. Returns 0 below 2^-1022 (no subnormal results) and +inf
-// from 2^1024 on.
+// from 2^1024 on, for any finite s.
 __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer
   const double t = fma(-s, EXPT_INV_L, shifter);
@@ -100,12 +116,12 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   q = fma(q, r, EXPT_C2);
   q = fma(q, r, 1.0);
   q = fma(q, r, 1.0);
-  const int e = n >> EXPT_BITS;
+  const int e = exp_scale_exponent(t, n);
   const long long bits =
       __double_as_longlong(tab[n & (EXPT_N - 1)]) + ((long long)e << 52);
-  double sc = __longlong_as_double(bits);
-  sc = e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : sc);
-  return q * sc;
+  const double v = q * __longlong_as_double(bits);
+  // out of range: the limits themselves (q need not be finite there)
+  return e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : v);
 }
 
 // exp(-s) for the FP32 form's residual evaluations, which need ~1e-13
@@ -122,12 +138,12 @@ __device__ __forceinline__ double exp_neg_refine(double s, const double* tab) {
   double q = fma(r, EXPT_C3, EXPT_C2);
   q = fma(q, r, 1.0);
   q = fma(q, r, 1.0);
-  const int e = n >> EXPT_BITS;
+  const int e = exp_scale_exponent(t, n);
   const long long bits =
       __double_as_longlong(tab[n & (EXPT_N - 1)]) + ((long long)e << 52);
-  double sc = __longlong_as_double(bits);
-  sc = e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : sc);
-  return q * sc;
+  const double v = q * __longlong_as_double(bits);
+  // out of range: the limits themselves (q need not be finite there)
+  return e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : v);
 }
 
 // Packed lower triangle of the 8x8 Jacobian: entry (a, b), b <= a.
@@ -386,8 +402,17 @@ __device__ __forceinline__ void shift_multipliers(const R l[NM], R dx, R dy, R o
 // the Maxwellian; on success fc holds the factor of the Jacobian at the
 // returned multipliers. Returns NEWTON_OK or NEWTON_SINGULAR (non-finite
 // values or a non-positive pivot).
+//
+// Written as one loop with a single evaluation pass and a single
+// factorisation, so that the unrolled pass (21 exponentials and the 44 sums)
+// exists once in the code: each turn evaluates the point `lc` and then acts
+// on it according to why it was evaluated (a start, a line-search trial, the
+// full step taken near the root). The points evaluated and the steps
+// accepted are those of the plain formulation: start, then per Newton step
+// the factor and direction at the accepted point and an Armijo line search.
 static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, int maxit, bool warm,
                                                float lam[NM], Fact32& fc, int* iters) {
+  enum { START_WARM, START_MAXWELL, TRIAL, FULL_STEP };
   *iters = 0;
   float m[NM];
   {
@@ -396,55 +421,83 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
     m[3] = fmaf(ubx, ubx, T); m[4] = ubx * uby; m[5] = fmaf(uby, uby, T);
     m[6] = ubx * fmaf(4.0f, T, u2); m[7] = uby * fmaf(4.0f, T, u2);
   }
-  PassGH32 ps;
-  if (warm) {
-    visit_groups<float>(lam, ps);
-    warm = isfinite(ps.F()) && ps.F() > 0.0f;
-  }
-  if (!warm) {
-    // Maxwellian multipliers; lambda_0 from the normalisation sum p = 1 (the
-    // pass at lambda_0 = 0 gives Z = F, and all its sums scale by 1/Z)
-    const float iT = 1.0f / T;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] = 0.0f;
-    lam[1] = -ubx * iT;
-    lam[2] = -uby * iT;
-    lam[3] = 0.5f * iT;
-    lam[5] = 0.5f * iT;
-    ps = PassGH32();
-    visit_groups<float>(lam, ps);
-    const float iz = 1.0f / ps.F();
-    lam[0] = logf(ps.F());
-    ps.scale(iz);
-  }
   auto dual = [&](const float* l, float F) {
 #pragma unroll
     for (int k = 0; k < NM; ++k) F = fmaf(l[k], m[k], F);
     return F;
   };
-  float Fd = dual(lam, ps.F());
-  float H[36];
-  int it = 0;
-  bool factored = false;
-  for (; it < maxit; ++it) {
-    float G[NM];
-    ps.assemble(G, H);
+  // Maxwellian multipliers with lambda_0 = 0 (fixed from the normalisation
+  // once evaluated)
+  auto maxwell = [&](float* l) {
+    const float iT = 1.0f / T;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) l[k] = 0.0f;
+    l[1] = -ubx * iT;
+    l[2] = -uby * iT;
+    l[3] = 0.5f * iT;
+    l[5] = 0.5f * iT;
+  };
+  float lc[NM], dl[NM];
+  int mode = START_WARM;
+  if (warm) {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lc[k] = lam[k];
+  } else {
+    maxwell(lc);
+    mode = START_MAXWELL;
+  }
+  float Fd = 0.0f, gd = 0.0f, t = 1.0f;
+  int it = 0, ls = 0;
+  for (;;) {
+    PassGH32 pc;
+    visit_groups<float>(lc, pc);
+    float F = pc.F();
+    if (mode == START_WARM) {
+      if (!(isfinite(F) && F > 0.0f)) {
+        maxwell(lc);
+        mode = START_MAXWELL;
+        continue;
+      }
+    } else if (mode == START_MAXWELL) {
+      // the pass at lambda_0 = 0 gives Z = F; all its sums scale by 1/Z
+      const float iz = 1.0f / F;
+      lc[0] = logf(F);
+      pc.scale(iz);
+      F = pc.F();
+    } else if (mode == TRIAL) {
+      const float Fc = dual(lc, F);
+      if (!(isfinite(Fc) && Fc <= Fd - 1e-4f * t * gd + 4e-7f * fabsf(Fd))) {
+        t *= 0.5f;
+        if (++ls >= 12) break;  // no acceptable step: fc is the factor at lam
+#pragma unroll
+        for (int k = 0; k < NM; ++k) lc[k] = fmaf(t, dl[k], lam[k]);
+        continue;
+      }
+      ++it;
+    } else if (!isfinite(F)) {  // FULL_STEP
+      return NEWTON_SINGULAR;
+    }
+    // accepted point: the Newton step there
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = lc[k];
+    Fd = dual(lam, F);
+    float G[NM], H[36];
+    pc.assemble(G, H);
     float gmax = 0.0f;
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
       G[k] -= m[k];
       gmax = fmaxf(gmax, fabsf(G[k]));
     }
-    if (!isfinite(gmax)) return NEWTON_SINGULAR;
-    if (!factor32(H, fc)) return NEWTON_SINGULAR;
-    factored = true;
-    if (gmax <= 2e-7f) break;
-    float dl[NM];
+    if (!isfinite(gmax) || !factor32(H, fc)) return NEWTON_SINGULAR;
+    if (mode == FULL_STEP || gmax <= 2e-7f || it >= maxit) break;
     solve32(fc, G, dl);
-    float gd = 0.0f;
+    gd = 0.0f;
 #pragma unroll
     for (int k = 0; k < NM; ++k) gd = fmaf(G[k], dl[k], gd);
     if (!(gd > 0.0f)) break;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lc[k] = lam[k] + dl[k];
     if (gd <= 2e-6f * fmaxf(1.0f, fabsf(Fd))) {
       // The predicted decrease gd/2 of the dual lies below its FP32 resolution:
       // a line search would only compare rounding noise. This close to the root
@@ -453,43 +506,15 @@ static __device__ __noinline__ int newton_fp32(float ubx, float uby, float T, in
       // residual, so it gets the factor of the Jacobian at the new multipliers
       // (one more FP32 pass): a factor one step old costs about one more FP64
       // residual per solve.
-#pragma unroll
-      for (int k = 0; k < NM; ++k) lam[k] += dl[k];
+      mode = FULL_STEP;
       ++it;
-      PassGH32 pn;
-      visit_groups<float>(lam, pn);
-      float Gn[NM];
-      pn.assemble(Gn, H);
-      if (!(isfinite(pn.F()) && factor32(H, fc))) return NEWTON_SINGULAR;
-      break;
+    } else {
+      mode = TRIAL;
+      t = 1.0f;
+      ls = 0;
     }
-    float t = 1.0f, lc[NM];
-    bool acc = false;
-    for (int ls = 0; ls < 12; ++ls) {
-#pragma unroll
-      for (int k = 0; k < NM; ++k) lc[k] = fmaf(t, dl[k], lam[k]);
-      PassGH32 pc;
-      visit_groups<float>(lc, pc);
-      const float Fc = dual(lc, pc.F());
-      if (isfinite(Fc) && Fc <= Fd - 1e-4f * t * gd + 4e-7f * fabsf(Fd)) {
-        acc = true;
-        ps = pc;
-        Fd = Fc;
-        break;
-      }
-      t *= 0.5f;
-    }
-    factored = false;
-    if (!acc) break;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] = lc[k];
   }
   *iters = it;
-  if (!factored) {
-    float G[NM];
-    ps.assemble(G, H);
-    if (!factor32(H, fc)) return NEWTON_SINGULAR;
-  }
   return NEWTON_OK;
 }
 
