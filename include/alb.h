@@ -249,8 +249,10 @@ int alb_totals(alb_handle* h, double* out);
  *   stream: cudaStream_t (NULL: the legacy default stream); asynchronous.
  * The partial sums live in a 128 KB static device array that every GPU that
  * loads the library holds until the process exits; nothing is allocated or
- * freed. The first call on a device looks up the array's device address with
- * that device current: make that first call before any stream capture.
+ * freed. Every call looks up the array's device address on the current
+ * device (a host-side query, so a device reset between calls is harmless); the
+ * first call on a device may load the library's device code there: make that
+ * first call before any stream capture.
  * Calls share the array: calls that overlap on the GPU (other streams, other
  * threads) race and give wrong sums; serialise them. Each call writes every
  * partial it reads, so no state carries over between calls. Same chunking

@@ -4,7 +4,6 @@
 // TOT_CHUNK nodes, one block per chunk; every block writes its four partial
 // sums to a scratch array, and one block then adds the partials in index
 // order. The result depends only on n, never on the launch configuration.
-#include <mutex>
 
 #include "alb_internal.h"
 
@@ -106,34 +105,23 @@ cudaError_t launch_totals(const FlowDev& f, double* partials, double* out, cudaS
 // The partial sums live in a file-scope device array instead of memory from
 // cudaMalloc. Every GPU that loads this library holds the array until the
 // process exits. In host code the array's name is only a host-side stand-in
-// for the symbol, so its device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// for the symbol, so its device address is looked up with cudaGetSymbolAddress
+// (on the current device) and passed to the kernels. The lookup is repeated on
+// every call: it is a host-side query, and an address kept from an earlier
+// call would point at unmapped memory after a device reset reloads the module.
 
 constexpr int NOALLOC_MAX_CHUNKS = 4096;  // up to 4096 * 65536 = 268,435,456 nodes
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_CHUNKS * 4];
 
-static double* g_noalloc_addr[NOALLOC_MAX_DEVICES];
-static std::mutex g_noalloc_mutex;
-
 long long noalloc_max_nodes() { return (long long)NOALLOC_MAX_CHUNKS * TOT_CHUNK; }
 
-// Device address of the scratch array on the current device (looked up on the
-// first call per device).
+// Device address of the scratch array on the current device.
 static cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  double* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
