@@ -16,6 +16,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 GAMMA = 1.4
+# strength of the batched and served vortices (the Shu vortex's beta) and
+# their hottest background temperature
+VORTEX_STRENGTH = 5.0
+VORTEX_T_MAX = 1.2
 
 
 def conserved(rho, ux, uy, T, gamma=GAMMA):
@@ -35,12 +39,15 @@ def isentropic_vortex(nx=64, ny=64, strength=5.0, radius=5.0, mach=1.2, rho_inf=
                       T_inf=1.0, noise=1e-3, seed=1, gamma=GAMMA):
     """Shu-type isentropic vortex centred in the box, carried by a uniform
     x-flow at the given Mach number, plus seeded uniform density noise
-    (u and T kept, so the noise is an entropy perturbation)."""
+    (u and T kept, so the noise is an entropy perturbation). At a background
+    temperature T_inf the vortex's velocities scale with sqrt(T_inf) and its
+    temperatures with T_inf (the same vortex in units of the background's
+    sound speed), so that it stays isentropic and in balance."""
     y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
     xc, yc = nx / 2.0, ny / 2.0
     xb, yb = (x - xc) / radius, (y - yc) / radius
     r2 = xb * xb + yb * yb
-    amp = strength / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    amp = strength / (2.0 * math.pi) * math.sqrt(T_inf) * np.exp(0.5 * (1.0 - r2))
     u_inf = mach * math.sqrt(gamma * T_inf)
     ux = u_inf - amp * yb
     uy = amp * xb
@@ -155,19 +162,42 @@ class FlowSpec:
     precision: str = "fp32"   # "fp32" | "fp64"
     seed: int = 0
     arrival: float = 0.0      # seconds from the start of a serving run
-    clamped: bool = False     # velocity clamped to keep the lattice realizable
+    clamped: bool = False     # velocity or temperature clamped to keep the lattice realizable
+
+    def __post_init__(self):
+        # The fastest velocity of the flow stays below |u| = 2.5: the carrier
+        # velocity (Mach times the background's sound speed) is clamped; this
+        # clamp and a vortex's temperature clamp are recorded.
+        if self.kind == "vortex":
+            T_inf = self.vortex_T_inf()
+            self.clamped = T_inf != 0.35 * self.T_ratio
+            c = math.sqrt(GAMMA * T_inf)
+            u_max = 2.5 - VORTEX_STRENGTH / (2.0 * math.pi) * math.sqrt(T_inf)
+        elif self.kind == "shear":
+            c = math.sqrt(GAMMA * 0.35)
+            u_max = 2.5
+        else:
+            return
+        if self.mach * c > u_max:
+            self.mach = u_max / c
+            self.clamped = True
+
+    def vortex_T_inf(self, gamma=GAMMA):
+        """Background temperature of a vortex: 0.35 times the temperature
+        ratio (the shear layer's hot stream), kept within [0.35 / 0.754, 1.2]:
+        the core (0.754 T_inf for strength 5) no colder than the shear
+        layer's cold stream, 0.35, and the background no hotter than the
+        hottest vortex the lattice carries at Mach 1.2-3 with no failed
+        rebuild in the oracle (1.3 gives one)."""
+        core = 1.0 - (gamma - 1.0) * VORTEX_STRENGTH ** 2 / (8.0 * gamma * math.pi ** 2) * math.e
+        return min(max(0.35 * self.T_ratio, 0.35 / core), VORTEX_T_MAX)
 
     def fields(self, gamma=GAMMA):
         if self.kind == "vortex":
-            T_inf = 0.35 * self.T_ratio
-            swirl = 5.0 / (2.0 * math.pi)
-            u_inf = self.mach * math.sqrt(gamma * T_inf)
-            if u_inf > 2.5 - swirl:
-                u_inf = 2.5 - swirl
-            mach = u_inf / math.sqrt(gamma * T_inf)
             r = max(5.0, min(self.nx, self.ny) / 12.8)
-            return isentropic_vortex(self.nx, self.ny, strength=5.0, radius=r, mach=mach,
-                                     T_inf=T_inf, seed=self.seed, gamma=gamma)
+            return isentropic_vortex(self.nx, self.ny, strength=VORTEX_STRENGTH, radius=r,
+                                     mach=self.mach, T_inf=self.vortex_T_inf(gamma),
+                                     seed=self.seed, gamma=gamma)
         if self.kind == "shear":
             return shear_layer(self.nx, mach=self.mach, T_cold=0.35, T_ratio=self.T_ratio,
                                delta=8.0, seed=self.seed, gamma=gamma,
@@ -191,14 +221,7 @@ def batched_flows(count=256, seed=4, smin=64, smax=1024, steps=500):
         mach = rng.uniform(0.5, 3.0)
         ratio = rng.uniform(1.0, 4.0)
         nu = math.exp(rng.uniform(math.log(1e-5), math.log(1e-3)))
-        spec = FlowSpec(kind, side, side, mach, ratio, nu, steps, "fp32", seed=1000 + k)
-        if kind == "shear":
-            # the shear layer's cold stream must stay below |u| = 2.5
-            u0 = mach * math.sqrt(GAMMA * 0.35)
-            if u0 > 2.5:
-                spec.mach = 2.5 / math.sqrt(GAMMA * 0.35)
-                spec.clamped = True
-        out.append(spec)
+        out.append(FlowSpec(kind, side, side, mach, ratio, nu, steps, "fp32", seed=1000 + k))
     return out
 
 
@@ -222,10 +245,7 @@ def serving_requests(rate=50.0, duration=60.0, seed=5, smin=64, smax=2048, steps
         mach = rng.uniform(0.5, 3.0)
         ratio = rng.uniform(1.0, 4.0)
         nu = math.exp(rng.uniform(math.log(1e-5), math.log(1e-3)))
-        spec = FlowSpec(kind, side, side, mach, ratio, nu, steps, prec, seed=2000 + k, arrival=t)
-        if kind == "shear" and mach * math.sqrt(GAMMA * 0.35) > 2.5:
-            spec.mach = 2.5 / math.sqrt(GAMMA * 0.35)
-            spec.clamped = True
-        out.append(spec)
+        out.append(FlowSpec(kind, side, side, mach, ratio, nu, steps, prec, seed=2000 + k,
+                            arrival=t))
         k += 1
     return out
