@@ -11,9 +11,13 @@ the initial state.
 
 Reported beside it: the FP64 plain path on the same flow (MLUPS and the FP32
 form's moment error against it), the same FP32 flow once developed (steps
-1900-2000 of the workload's 2000), the end-to-end figure through the C ABI
-with host buffers, the FP64-pipe roofline of the step kernel, and the CPU
-oracle on a bounded sample of the same flow.
+1900-2000 of the workload's 2000) and the mean over all its steps after the
+warm-up, the FP32 form's moment error against the FP64 oracle on the 256^2
+version of the flow over 200 steps (free-running and with replayed lattice
+decisions), the end-to-end figure through the C ABI with host buffers, the
+FP64-pipe roofline of the step kernel with the method's own minimum FP64
+work beside it, and the CPU oracle on a bounded sample of the same flow (all
+cores and one core, CPU model recorded).
 
 Two sub-results run after it on one GPU (skipped under torchrun with N > 1):
 
@@ -84,6 +88,8 @@ def parse():
                     help="advance the FP32 flow to this step and time the last 100 "
                          "(0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-error", action="store_true",
+                    help="skip the FP32 form's error against the oracle at 256^2")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-overlap", action="store_true")
@@ -208,53 +214,114 @@ def workload_config(n, world):
 
 # ----------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(n, steps, warmup=1):
-    """The CPU oracle on a bounded sample of the n^2 shear layer: a 64-row band
-    of the uniform hot stream and a 64-row band centred on a shear layer, each
-    n wide with zero-gradient ends in y. Their per-node times are weighted by
-    the full flow's row mix (128 of n rows lie in the two layers)."""
+def cpu_model():
+    """The host CPU's model name (lscpu), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _omp():
+    """The OpenMP runtime the oracle runs on (its thread count can be set)."""
+    import ctypes
+    try:
+        return ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+
+
+def oracle_sample(n, steps, warmup=1, rows=None, threads=None):
+    """The CPU oracle on a bounded sample of the n^2 shear layer: a band of
+    `rows` rows of the uniform hot stream and one centred on a shear layer,
+    each n wide with zero-gradient ends in y. A sample step is one oracle step
+    of both bands. Reported: the measured time per sample step, the sample's
+    own rate, and the rate of the full flow estimated by weighting the two
+    bands' per-node times by the flow's row mix (2 * rows of n rows lie in
+    the two layers)."""
     import oracle as O
-    f = flows.shear_layer(n)
-    rows = min(64, max(8, n // 8))
-    bands = {"uniform": 0, "layer": n // 4 - rows // 2}
-    per_node = {}
-    total_time = 0.0
-    for name, y0 in bands.items():
-        band = [a[y0:y0 + rows].copy() for a in f]
-        s = O.Simulation(O.make_config(n, rows, umax=2, nu=NU, bc_y=O.ZERO_GRADIENT,
-                                            sensor=bool(SENSOR)))
-        assert s.init(*band) == O.OK
-        if warmup:
-            s.step(warmup)
-        t0 = time.perf_counter()
-        s.step(steps)
-        dt = time.perf_counter() - t0
-        total_time += dt
-        per_node[name] = dt / (steps * n * rows)
+    O.lib()
+    omp = _omp()
+    if threads and omp is not None:
+        omp.omp_set_num_threads(int(threads))
+    used = omp.omp_get_max_threads() if omp is not None else os.cpu_count()
+    try:
+        f = flows.shear_layer(n)
+        rows = rows or min(64, max(8, n // 8))
+        bands = {"uniform": 0, "layer": n // 4 - rows // 2}
+        sims = {}
+        for name, y0 in bands.items():
+            band = [a[y0:y0 + rows].copy() for a in f]
+            s = O.Simulation(O.make_config(n, rows, umax=2, nu=NU, bc_y=O.ZERO_GRADIENT,
+                                           sensor=bool(SENSOR)))
+            assert s.init(*band) == O.OK
+            sims[name] = s
+        for s in sims.values():
+            if warmup:
+                s.step(warmup)
+        per = {k: 0.0 for k in sims}
+        for _ in range(steps):
+            for name, s in sims.items():
+                t0 = time.perf_counter()
+                s.step(1)
+                per[name] += time.perf_counter() - t0
+    finally:
+        if threads and omp is not None:
+            omp.omp_set_num_threads(os.cpu_count() or 1)
+    total = sum(per.values())
     frac_layer = min(1.0, 2 * rows / n)
-    t_node = (1 - frac_layer) * per_node["uniform"] + frac_layer * per_node["layer"]
-    return {"mlups": 1e-6 / t_node, "time_s": total_time,
-            "sample": "two %dx%d bands (uniform stream; shear layer), %d steps each, per-node "
-                      "times weighted by the %d^2 flow's row mix" % (n, rows, steps, n)}
+    t_node = ((1 - frac_layer) * per["uniform"] + frac_layer * per["layer"]) / (steps * n * rows)
+    nodes = 2 * n * rows
+    return {"mlups": 1e-6 / t_node, "mlups_sample": nodes * steps / total / 1e6,
+            "time_s": total, "ms_per_step": 1e3 * total / steps, "nodes_per_step": nodes,
+            "threads": used,
+            "sample": "two %dx%d bands of the %d^2 shear layer (uniform stream; shear layer), "
+                      "zero-gradient ends in y, %d timed steps each after %d untimed; value "
+                      "weights their per-node times by the full flow's row mix"
+                      % (n, rows, n, steps, warmup)}
+
+
+def cpu_baseline(n):
+    """The oracle on all host cores (two 64-row bands, 2 steps) and on one core
+    (two 8-row bands, 1 step): a bounded sample of a few seconds each."""
+    allc = oracle_sample(n, 2, warmup=1)
+    one = oracle_sample(n, 1, warmup=1, rows=8, threads=1)
+    return {"value": round(allc["mlups"], 4), "unit": UNIT, "cores": allc["threads"],
+            "kind": "oracle", "sample": allc["sample"], "cpu_model": cpu_model(),
+            "nproc": os.cpu_count(), "timed_s": round(allc["time_s"], 2),
+            "single_thread": {"value": round(one["mlups"], 5), "unit": UNIT, "cores": 1,
+                              "sample": one["sample"], "timed_s": round(one["time_s"], 2)}}
 
 
 # ----------------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands on the host cores. Each
+    step is one oracle step of the bounded sample above (two 64-row bands of
+    the 4096^2 flow); ms_per_step is the measured time of that sample step,
+    and the value is the full flow's rate estimated from it."""
     if rank != 0:
         return
-    cores = os.cpu_count()
     t0 = time.perf_counter()
-    res = oracle_sample(args.n, max(1, args.steps // 10), warmup=min(1, args.warmup))
+    res = oracle_sample(args.n, args.steps, warmup=args.warmup)
+    cpu = {"value": round(res["mlups"], 4), "unit": UNIT, "cores": res["threads"],
+           "kind": "oracle", "sample": res["sample"], "cpu_model": cpu_model(),
+           "nproc": os.cpu_count()}
     line = {
         "metric": METRIC, "value": round(res["mlups"], 4), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "impl": "reference",
-        "ms_per_step": round(1e3 * args.n * args.n / (res["mlups"] * 1e6), 1),
+        "ms_per_step": round(res["ms_per_step"], 1),
+        "step": "one oracle step of the sample (%d node updates)" % res["nodes_per_step"],
+        "sample_mlups": round(res["mlups_sample"], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": workload_config(args.n, world),
-        "cpu_baseline": {"value": round(res["mlups"], 4), "unit": UNIT, "cores": cores,
-                         "kind": "oracle", "sample": res["sample"]},
+        "cpu_baseline": cpu,
         "e2e": {"value": round(res["mlups"], 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "wall_s": round(time.perf_counter() - t0, 1),
@@ -271,6 +338,51 @@ def _sync_flagged(obj, alb):
     except alb.AlbError as e:
         if e.code != alb.ALB_ENEWTON:
             raise
+
+
+def shear_error_vs_oracle(alb, n=256, steps=200):
+    """The FP32 form against the FP64 oracle on the n^2 version of the headline
+    flow over `steps` steps: free-running, and with the oracle replaying the
+    GPU's lattice decisions (which isolates the step's arithmetic). Also the
+    lattice decisions the GPU took differently from what Eq. criterion gives on
+    the replayed oracle's moments (FP32 round-off at a threshold)."""
+    import oracle as O
+    fields = flows.shear_layer(n)
+    okw = dict(umax=2, nu=NU, sensor=bool(SENSOR))
+    fl = alb.Flow(n, n, u_max=2, nu=NU, precision=alb.ALB_FP32_FORM, sensor=SENSOR)
+    fl.init(*fields)
+    rep = O.Simulation(O.make_config(n, n, **okw))
+    assert rep.init(*fields) == O.OK
+    crit = lambda u: np.clip(np.ceil(u + 0.5) - 1, -2, 2).astype(np.int8)
+    flips = 0
+    for _ in range(steps):
+        _, ux, uy, _ = rep.primitives()
+        fl.step(1)
+        gx, gy = fl.shifts()
+        flips += int((gx != crit(ux)).sum() + (gy != crit(uy)).sum())
+        rep.step_forced(gx, gy)
+    got = fl.moments()
+    fl.close()
+    free = O.Simulation(O.make_config(n, n, **okw))
+    assert free.init(*fields) == O.OK
+    free.step(steps)
+
+    def errs(ref):
+        r, a, b, e = got
+        R, A, B, E = ref
+        dm, mm = np.sqrt((a - A) ** 2 + (b - B) ** 2), np.sqrt(A ** 2 + B ** 2)
+        mx = max(np.abs(r - R).max() / np.abs(R).max(), dm.max() / mm.max(),
+                 np.abs(e - E).max() / np.abs(E).max())
+        l2 = max(np.linalg.norm(r - R) / np.linalg.norm(R),
+                 np.linalg.norm(dm) / np.linalg.norm(mm),
+                 np.linalg.norm(e - E) / np.linalg.norm(E))
+        return {"max_rel": float("%.3e" % mx), "l2_rel": float("%.3e" % l2)}
+
+    return {"workload": "shear layer %dx%d (the headline's recipe), %d steps, FP32 form "
+                        "against the FP64 oracle" % (n, n, steps),
+            "replayed": errs(rep.moments()), "free_running": errs(free.moments()),
+            "flipped_decisions": flips,
+            "flipped_per_node_step": float("%.3e" % (flips / (n * n * steps)))}
 
 
 def run_batched(args):
@@ -568,12 +680,19 @@ def run_ours(args, world, rank, local):
     # rolled-up layers need more FP32 Newton steps and refinements per node.
     developed = None
     k_dev = 100
+    full_run = None
     if args.developed_steps >= total32 + k_dev:
         clocks_d = ClockSampler(local)
         adv = args.developed_steps - k_dev - total32
+        ea0 = torch.cuda.Event(enable_timing=True)
+        ea1 = torch.cuda.Event(enable_timing=True)
+        ea0.record(stream)
         for _ in range(adv // 100):
             alb.alb_step(fl32.h, 100)
-        ms_a, _ = timed(fl32, 0, adv % 100)
+        alb.alb_step(fl32.h, adv % 100)
+        ea1.record(stream)
+        torch.cuda.synchronize()
+        ms_adv = ea0.elapsed_time(ea1)
         clocks_d.start()
         ms_d, dd = timed(fl32, k_dev, 0)
         clk_d = clocks_d.stop()
@@ -600,6 +719,14 @@ def run_ours(args, world, rank, local):
         developed["state"] = {"finite": bool(np.isfinite(r).all() and np.isfinite(e).all()),
                               "rho_min": float("%.4g" % r.min()),
                               "T_min": float("%.4g" % T.min())}
+        # every step of the workload after the warm-up, timed in three pieces
+        # with CUDA events on the flow's stream: the headline steps, the
+        # advance, the developed steps
+        k_all = args.steps + adv + k_dev
+        ms_all = dist_max(ms32 + ms_adv + ms_d, world)
+        full_run = {"value": round(aggregate_mlups(world, N, k_all, ms_all), 2), "unit": UNIT,
+                    "steps": [args.warmup, args.developed_steps],
+                    "ms_per_step": round(ms_all / k_all, 3)}
     st = fl32.stats()
     fl32.close()
 
@@ -682,9 +809,11 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        res = oracle_sample(n, 2, warmup=1)
-        cpu = {"value": round(res["mlups"], 4), "unit": UNIT, "cores": os.cpu_count(),
-               "kind": "oracle", "sample": res["sample"]}
+        cpu = cpu_baseline(n)
+
+    err256 = None
+    if rank == 0 and not args.no_oracle_error:
+        err256 = shear_error_vs_oracle(alb)
 
     batched = serve = None
     if world == 1 and not args.no_batched:
@@ -710,6 +839,7 @@ def run_ours(args, world, rank, local):
                      "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "kernel": "step_kernel<float>",
                      "fp64_slots_per_node": round(slots / args.steps / N, 1),
+                     "method_floor": costmodel.method_floor(mlups / world),
                      "hbm": {"achieved_gbs": round(hbm_gbs, 1),
                              "bytes_per_node": costmodel.BYTES_PER_NODE["fp32"]}},
         "clocks": clk,
@@ -720,6 +850,10 @@ def run_ours(args, world, rank, local):
                                         "newton_failures", "reconstruction_failures")},
     }
     line.update(extra)
+    if err256:
+        line.setdefault("error", {})["oracle_256"] = err256
+    if full_run:
+        line["full_run"] = full_run
     if developed:
         line["developed_flow"] = developed
     if ovl:

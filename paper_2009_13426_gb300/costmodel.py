@@ -157,6 +157,19 @@ def fp64_slots(stats: dict, precision: str) -> float:
     return CALIBRATION[precision] * raw
 
 
+def method_floor(mlups: float) -> dict:
+    """The method's own minimum FP64 work per node update, beside the count of
+    what the kernel executes: one FP64 evaluation of the equilibrium (the
+    grouped exponents of the 21 velocities, their table exponentials, the 8
+    constraint sums), the least a solve needs to confirm max|G|/rho <= 1e-12
+    in FP64 (App. C.1). Returns that count, the MLUPS the FP64 pipe would
+    allow if it were all the work, and the fraction of it `mlups` reaches."""
+    slots = 55 + 21 * 7 + 68
+    cap = FP64_PEAK_TFLOPS * 1e12 / 2.0 / slots / 1e6
+    return {"fp64_slots_per_node": slots, "mlups_at_fp64_peak": round(cap, 1),
+            "frac": round(mlups / cap, 4)}
+
+
 def describe():
     return {
         "plain_eval": round(plain_eval(), 1),
