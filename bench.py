@@ -454,10 +454,8 @@ def run_batched(args):
                          "rebuild": tot["reconstruction_failures"],
                          "node_per_update": float("%.3g" % (tot["newton_failures"] / upd)),
                          "rebuild_per_rebuild": float("%.3g" % (
-                             tot["reconstruction_failures"] / max(tot["reconstructions"], 1))),
-                         "note": "fallbacks near the lattice's operability range; the CPU "
-                                 "oracle reports rebuild fallbacks on the same vortex initial "
-                                 "states (low core temperature, high Mach)"}}
+                             tot["reconstruction_failures"] / max(tot["reconstructions"], 1)))},
+            "clamped_flows": sum(1 for sp in specs if sp.clamped)}
 
 
 def _serve_stream(alb, reqs, window, drain):
@@ -543,6 +541,8 @@ def _flag_detail(alb, ids, done):
         upd = sum(r["stats"]["node_updates"] for r in rs)
         reb = sum(r["stats"]["reconstructions"] for r in rs)
         out[kind] = {"completed": len(rs),
+                     "clamped": sum(1 for rid in done if ids[rid].kind == kind and
+                                    ids[rid].clamped),
                      "flagged": sum(1 for r in rs if r["status"] == alb.ALB_ENEWTON),
                      "with_node_failures": sum(1 for r in rs if r["stats"]["newton_failures"]),
                      "node_failures_per_update": float("%.3g" % (

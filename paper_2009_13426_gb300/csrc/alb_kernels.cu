@@ -267,7 +267,7 @@ static dim3 step_grid(const Params& p, int* lg) {
   int l = 3;
   while (l < StepShape<P>::LOG2B && (1 << l) < p.nx) ++l;
   *lg = l;
-  const int rows = StepShape<P>::B >> l;
+  const int rows = (1 << StepShape<P>::LOG2B) >> l;
   return dim3((p.nx + (1 << l) - 1) >> l, (p.ny + rows - 1) / rows);
 }
 
