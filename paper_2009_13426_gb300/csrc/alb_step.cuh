@@ -233,8 +233,8 @@ __device__ __forceinline__ void store_shakhov(const Params& pr, const P* st, con
     const P cx = (P)XI_X(i) - bx, cy = (P)XI_Y(i) - by;
     const P c2 = cx * cx + cy * cy;
     const P qc = qx * cx + qy * cy;
-    pop_out[i * ps + k] = fma(om, fe - f, f) + af * qc * (c2 * h - cp) * fe;
-    pop_out[(Q + i) * ps + k] = fma(om, ge - g, g) + ag * qc * ge;
+    __stcs(&pop_out[i * ps + k], fma(om, fe - f, f) + af * qc * (c2 * h - cp) * fe);
+    __stcs(&pop_out[(Q + i) * ps + k], fma(om, ge - g, g) + ag * qc * ge);
   }
 }
 
@@ -320,8 +320,8 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
         const P ge = gp * fe;
         const P f = st[i * B];
         const P g = st[(Q + i) * B];
-        pop_out[i * ps + k] = fma(om, fe - f, f);
-        pop_out[(Q + i) * ps + k] = fma(om, ge - g, g);
+        __stcs(&pop_out[i * ps + k], fma(om, fe - f, f));
+        __stcs(&pop_out[(Q + i) * ps + k], fma(om, ge - g, g));
       }
     }
   } else {
@@ -413,8 +413,11 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
       const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
       const size_t ks = (size_t)ry * pr.nx + rx;
       if (!gh && a.lat_in[ks] == code) {
-        cl.pop[i * B] = a.pop_in[i * ps + ks];
-        cl.pop[(Q + i) * B] = a.pop_in[(Q + i) * ps + ks];
+        // populations are read once and written once per step: streaming
+        // (evict-first) loads and stores keep L2 for the lattice codes and
+        // the threads' stack
+        cl.pop[i * B] = __ldcs(&a.pop_in[i * ps + ks]);
+        cl.pop[(Q + i) * B] = __ldcs(&a.pop_in[(Q + i) * ps + ks]);
       } else {
         rq.entry[atomicAdd(&rq.count, 1)] = (unsigned short)((t << 5) | i);
       }

@@ -1,5 +1,5 @@
-"""Full-size parity: the 4096^2 shear layer in the launch configuration the
-benchmark times (one flow, step_kernel, 128-node row blocks). The GPU state
+"""Full-size parity: the 4096^2 shear layer in the configuration the benchmark
+times (one flow, step_kernel in its launch shape, kinetic sensor on). The GPU state
 after a few steps is exported; for sampled nodes the oracle's own node
 functions redo one step from it - pull in the lattice the node selected, Grad
 rebuild of every pull whose sender lives in another lattice
@@ -77,7 +77,7 @@ def export(fl):
 
 @pytest.mark.parametrize("precision,tol", [(1, 1e-5), (0, 1e-11)])
 def test_full_size_sampled_step(alb, fields, precision, tol):
-    fl = alb.Flow(N, N, u_max=2, nu=NU, precision=precision)
+    fl = alb.Flow(N, N, u_max=2, nu=NU, precision=precision, sensor=1)
     fl.init(*fields)
     fl.step(3)
     fl.sync()
@@ -89,7 +89,7 @@ def test_full_size_sampled_step(alb, fields, precision, tol):
     fl.close()
     # the lattice each node pulled into is the one it selected
     assert np.array_equal(lat1[0], before[4]) and np.array_equal(lat1[1], before[5])
-    cfg = O.make_config(N, N, umax=2, nu=NU)
+    cfg = O.make_config(N, N, umax=2, nu=NU, sensor=True)
     xi = O.velocities()
     rng = np.random.default_rng(11)
     # interface nodes: some pull comes from another lattice
