@@ -5,9 +5,10 @@
 //
 // The grid is persistent (resident blocks x SMs). A block takes work items,
 // each a tile of one flow (2^tw_log2 nodes along x by block >> tw_log2 rows),
-// either from an atomic counter or by a fixed stride. For every item the
-// block copies the flow's step arguments into shared memory (two barriers
-// per item), then each thread updates one node.
+// either from an atomic counter or by a fixed stride. When an item belongs to
+// another flow (or buffer) than the block's previous one, the block copies
+// that flow's step arguments into shared memory; then each thread updates
+// one node.
 #pragma once
 
 #include "alb_step.cuh"
@@ -30,6 +31,7 @@ __global__ void __launch_bounds__(B, MINB)
   const StepArgs<P>& a = *reinterpret_cast<const StepArgs<P>*>(s_args);
   const Columns<P, B> cl(smem_raw);
   int it = blockIdx.x;
+  int loaded = -1;  // (flow, buffer) whose arguments s_args holds
   for (;;) {
     __syncthreads();  // the previous item's readers of s_args / s_item are done
     if (counter) {
@@ -39,12 +41,19 @@ __global__ void __launch_bounds__(B, MINB)
     }
     if (it >= nitems) break;
     const WorkItem w = items[it];
-    if (threadIdx.x < sizeof(StepArgs<P>) / 8) {
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
-          args + 2 * (size_t)w.flow + (cur[w.flow] ^ parity));
-      s_args[threadIdx.x] = src[threadIdx.x];
+    // Items are laid out flow by flow, so consecutive items of a block mostly
+    // belong to one flow: copy its arguments only when the flow or buffer
+    // changes (the same decision in every thread of the block).
+    const int want = 2 * w.flow + (cur[w.flow] ^ parity);
+    if (want != loaded) {
+      if (threadIdx.x < sizeof(StepArgs<P>) / 8) {
+        const unsigned long long* src =
+            reinterpret_cast<const unsigned long long*>(args + want);
+        s_args[threadIdx.x] = src[threadIdx.x];
+      }
+      __syncthreads();
+      loaded = want;
     }
-    __syncthreads();
     NodeCount nc;
     tile_step<P, B>(a, w.x0, w.y0, w.tw_log2, cl, s_tab, s_rq, nc);
     flush_counts(a.ctr, nc);
