@@ -3,10 +3,12 @@ alpha, Sec. IV.A.2), of its second-order central differences (Sec. IV.A.1,
 through the Grad initial state of Eqs. GradGeneral_f / GradGeneral_g), and
 of the relaxation time of a rebuilt pull (Sec. III.B.2: the rebuilt
 population is the sender's post-collision one, so it relaxes with the
-sender's tau).
+sender's tau), and of the failure policy where the root finder fails (an
+uncollided node; the normalised Maxwellian-guess exponential for a rebuild).
 
-The last test plants each mistake these pins are meant to catch in a copy of
-the oracle's source, builds it, and checks that the pin fails on it."""
+test_planted_mistakes_fail_their_pins plants each mistake these pins are
+meant to catch in a copy of the oracle's source, builds it, and checks that
+the pin fails on it."""
 import math
 import os
 import subprocess
@@ -323,6 +325,14 @@ MUTANTS = [
      "const double tau_pr = 0.5 + (c->nu / c->prandtl) / s->T[k];",
      "const double tau_pr = 0.5 + (c->nu / c->prandtl) / s->T[y * c->nx + x];",
      T + "test_rebuilt_pull_relaxes_with_the_sender_tau"),
+    ("a failed node relaxed towards the failed equilibrium",
+     "for (int i = 0; i < Q; ++i) { fs[i] = f[i]; gs[i] = g[i]; }",
+     "for (int i = 0; i < Q; ++i) { fs[i] = 0.5 * (f[i] + feq[i]); gs[i] = g[i]; }",
+     T + "test_failed_collision_leaves_the_node_uncollided"),
+    ("fallback in the sender's lattice instead of the receiver's",
+     "const double ubx = s->ux[k] - Upx, uby = s->uy[k] - Upy, T = s->T[k];",
+     "const double ubx = s->ux[k], uby = s->uy[k] - Upy, T = s->T[k];",
+     T + "test_failed_rebuild_falls_back_to_the_normalised_maxwellian_exponential"),
 ]
 
 
@@ -350,3 +360,57 @@ def test_planted_mistakes_fail_their_pins(tmp_path):
         lib = obuild.compile_source(str(src), str(tmp_path / ("m%d.so" % j)))
         rc, out = _run_pin(lib, nodeid)
         assert rc == 1, (name, rc, out)
+
+
+# ---------------------------------------------------------------- failure policy
+
+def test_failed_collision_leaves_the_node_uncollided():
+    """Reading 11 (the paper is silent): a node whose root finder fails is not
+    collided, f* = f and g* = g exactly, and the failure is reported."""
+    cfg = O.make_config(4, 4, nu=1e-2, newton_maxit=0)
+    st, lam, feq, _ = O.equilibrium(1.1, 0.3, -0.2, 0.7)
+    rng = np.random.default_rng(3)
+    f = feq * (1 + 0.01 * rng.standard_normal(21))
+    g = (2 * CV - 2) * 0.7 * feq * (1 + 0.01 * rng.standard_normal(21))
+    st, fs, gs = O.collide_node(cfg, f, g, 1, 0)
+    assert st != O.OK
+    assert np.array_equal(fs, f) and np.array_equal(gs, g)
+
+
+def test_failed_rebuild_falls_back_to_the_normalised_maxwellian_exponential():
+    """Reading 11: a rebuilt pull whose root finder fails takes the Maxwellian
+    guess's exponential of the sender's state in the receiver's lattice,
+    f_i = rho exp(-|xi_i - ubar|^2 / (2T)) / sum_j exp(-|xi_j - ubar|^2 / (2T)),
+    ubar = u_sender - U', and g_i = (2 Cv - D) T f_i. Every node is forced
+    from lattice (0, 0) into (1, 0) with the root finder allowed no step, so
+    every pull is such a fallback."""
+    nx, ny = 6, 5
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    rho = 1.0 + 0.1 * np.sin(2 * math.pi * xx / nx)
+    T = 0.7 + 0.1 * np.cos(2 * math.pi * yy / ny)
+    ux = 0.2 * np.sin(2 * math.pi * yy / ny)
+    uy = 0.1 * np.cos(2 * math.pi * xx / nx)
+    init = O.Simulation(O.make_config(nx, ny, nu=1e-2))
+    assert init.init(*flows.conserved(rho, ux, uy, T)) == O.OK
+    f0, g0 = init.populations()
+    sx, sy = init.shifts()
+    sim = O.Simulation(O.make_config(nx, ny, nu=1e-2, newton_maxit=0))
+    sim.set_state(f0, g0, sx, sy)
+    r0, u0, v0, T0 = sim.primitives()
+    assert sim.step_forced(np.ones((ny, nx)), np.zeros((ny, nx))) == O.ENEWTON
+    st = sim.stats()
+    assert st["reconstructions"] == st["reconstruction_failures"] == 21 * nx * ny
+    f, g = sim.populations()
+    xi_x, xi_y = _xi()
+    err = 0.0
+    for j in range(ny):
+        for i in range(nx):
+            for q in range(21):
+                a = (i - (int(xi_x[q]) + 1)) % nx
+                b = (j - int(xi_y[q])) % ny
+                ubx, uby = u0[b, a] - 1.0, v0[b, a]
+                w = np.exp(-((xi_x - ubx) ** 2 + (xi_y - uby) ** 2) / (2 * T0[b, a]))
+                fe = r0[b, a] * w[q] / w.sum()
+                ge = (2 * CV - 2) * T0[b, a] * fe
+                err = max(err, abs(f[j, i, q] - fe) / fe, abs(g[j, i, q] - ge) / ge)
+    assert err <= 1e-13
