@@ -191,6 +191,28 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   return 0;
 }
 
+// The equilibrium column (FP64 values per unit density at stride B) in the
+// population precision. In the FP32 form every value is rounded to FP32 once,
+// in place, into the first word of its slot (the FP64 value is not read
+// again), so that the sensor, the BGK update and the App. E term read the
+// same float and the FP64 pipe converts each value once; element i is then
+// at [i * eq_stride<P, B>()].
+template <typename P, int B>
+__device__ __forceinline__ const P* eq_in_precision(double* eq) {
+  if constexpr (std::is_same<P, float>::value) {
+    float* v = reinterpret_cast<float*>(eq);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[2 * i * B] = (float)eq[i * B];
+    return v;
+  } else {
+    return eq;
+  }
+}
+template <typename P, int B>
+__host__ __device__ constexpr int eq_stride() {
+  return std::is_same<P, float>::value ? 2 * B : B;
+}
+
 // Store of a collided node for Pr != 1: BGK plus the heat-flux term of App. E
 // (Eqs. Shakhov, prandtlPoly),
 //   f* += (1/tau - 1/tau_Pr) q.cbar / (rho Cp T^2) (|cbar|^2 / (2T) - Cp) f^eq,
@@ -200,7 +222,7 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
 // `code`), tau_Pr = 1/2 + (nu/Pr)/T, both relaxation times scaled by the
 // sensor factor tau / (1/2 + nu/T).
 template <typename P, int B>
-__device__ __forceinline__ void store_shakhov(const Params& pr, const P* st, const double* eq,
+__device__ __forceinline__ void store_shakhov(const Params& pr, const P* st, const P* eqv,
                                               double rho, double ux, double uy, double T,
                                               int code, P tau, size_t k, size_t ps,
                                               P* __restrict__ pop_out) {
@@ -226,7 +248,7 @@ __device__ __forceinline__ void store_shakhov(const Params& pr, const P* st, con
   const P h = (P)0.5 / Tp;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const P fe = (P)eq[i * B] * rp;
+    const P fe = eqv[i * eq_stride<P, B>()] * rp;
     const P ge = gp * fe;
     const P f = st[i * B];
     const P g = st[(Q + i) * B];
@@ -300,23 +322,25 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
     const P gp = ((P)2 * (P)pr.cv - (P)2) * Tp;
     P tau = (P)0.5 + (P)pr.nu / Tp;
     const P rp = (P)rho;
+    const P* eqv = eq_in_precision<P, B>(cl.eq);
+    constexpr int es = eq_stride<P, B>();
     if (pr.sensor) {
       P eps = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const P fe = (P)cl.eq[i * B] * rp;
+        const P fe = eqv[i * es] * rp;
         eps += fabs(st[i * B] - fe) / fe;
       }
       eps /= (P)Q;
       tau *= sensor_alpha<P>(pr, eps);
     }
     if (pr.shakhov) {
-      store_shakhov<P, B>(pr, st, cl.eq, rho, ux, uy, T, code, tau, k, ps, pop_out);
+      store_shakhov<P, B>(pr, st, eqv, rho, ux, uy, T, code, tau, k, ps, pop_out);
     } else {
       const P om = (P)1 / tau;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const P fe = (P)cl.eq[i * B] * rp;
+        const P fe = eqv[i * es] * rp;
         const P ge = gp * fe;
         const P f = st[i * B];
         const P g = st[(Q + i) * B];
