@@ -88,3 +88,18 @@ def test_exports_are_consistent(alb):
     np.testing.assert_allclose(r * ux, A, rtol=1e-14, atol=1e-15)
     nsx, nsy = fl.next_shifts()
     assert nsx.min() >= -2 and nsx.max() <= 2 and nsy.min() >= -2 and nsy.max() <= 2
+
+
+def test_shear_case_saves_and_restores_the_developed_flow(alb, tmp_path, capsys):
+    """The profiling case (paper_2009_13426_gb300.shear_case): a checkpoint
+    saved after some steps and restored into a new flow continues exactly as
+    the flow that kept running (same counters per node over the next steps)."""
+    from paper_2009_13426_gb300 import shear_case
+    f = str(tmp_path / "case.npy")
+    shear_case.main(["--n", "64", "--advance", "30", "--steps", "0", "--save", f])
+    capsys.readouterr()
+    shear_case.main(["--n", "64", "--load", f, "--steps", "4"])
+    restored = capsys.readouterr().out.strip().splitlines()[-1]
+    shear_case.main(["--n", "64", "--advance", "30", "--steps", "4"])
+    straight = capsys.readouterr().out.strip().splitlines()[-1]
+    assert restored == straight
