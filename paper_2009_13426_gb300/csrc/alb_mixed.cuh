@@ -150,7 +150,8 @@ __device__ __forceinline__ double exp_neg_refine(double s, const double* tab) {
 __host__ __device__ constexpr int tri(int a, int b) { return a * (a + 1) / 2 + b; }
 
 // FP32 pass: F = sum p, G = sum p P and H = sum p P P^T at the visited
-// multipliers, accumulated velocity by velocity (compile-time monomials).
+// multipliers, accumulated group by group of the velocity set (compile-time
+// monomials).
 struct PassGH32 {
   float Fs, Gs[NM], Hs[36];
   __device__ __forceinline__ PassGH32() {
@@ -171,11 +172,50 @@ struct PassGH32 {
     }
   }
   __device__ __forceinline__ void rest(float s) { point<0>(expf(-s)); }
+  // A symmetric pair enters through the sum S and difference D of its two
+  // points: every sum takes c S or c D, with c the compile-time value of the
+  // monomial (product) at the first point and D where the second point flips
+  // its sign (the grouping of the FP64 Jacobian, jac_pair).
   template <int A, int AX, int IP, int IM>
-  __device__ __forceinline__ void pair(float sp, float sm) { point<IP>(expf(-sp)); point<IM>(expf(-sm)); }
+  __device__ __forceinline__ void pair(float sp, float sm) {
+    const float pp = expf(-sp), pm = expf(-sm);
+    const float S = pp + pm, D = pp - pm;
+    Fs += S;
+#pragma unroll
+    for (int a = 0; a < NM; ++a) {
+      const int ca = PM(a, IP);
+      if (ca != 0) Gs[a] = madd(Gs[a], PM(a, IM) == ca ? S : D, ca);
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        const int c = PM(a, IP) * PM(b, IP);
+        if (c != 0) Hs[tri(a, b)] = madd(Hs[tri(a, b)], PM(a, IM) * PM(b, IM) == c ? S : D, c);
+      }
+    }
+  }
+  // A diagonal quadruple enters through its four parity combinations (even
+  // or odd in x, even or odd in y), as in jac_quad.
   template <int A, int IPP, int IMP, int IMM, int IPM>
   __device__ __forceinline__ void quad(float spp, float smp, float smm, float spm) {
-    point<IPP>(expf(-spp)); point<IMP>(expf(-smp)); point<IMM>(expf(-smm)); point<IPM>(expf(-spm));
+    const float ppp = expf(-spp), pmp = expf(-smp), pmm = expf(-smm), ppm = expf(-spm);
+    const float Ap = ppp + ppm, Bm = pmp + pmm, Cp = ppp - ppm, Dm = pmp - pmm;
+    const float ee = Ap + Bm, oe = Ap - Bm, eo = Cp + Dm, oo = Cp - Dm;
+    Fs += ee;
+#pragma unroll
+    for (int a = 0; a < NM; ++a) {
+      const int ca = PM(a, IPP);
+      if (ca != 0) {
+        const bool xo = PM(a, IMP) == -ca, yo = PM(a, IPM) == -ca;
+        Gs[a] = madd(Gs[a], xo ? (yo ? oo : oe) : (yo ? eo : ee), ca);
+      }
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        const int c = PM(a, IPP) * PM(b, IPP);
+        if (c == 0) continue;
+        const bool xo = PM(a, IMP) * PM(b, IMP) == -c;  // x -> -x flips the sign
+        const bool yo = PM(a, IPM) * PM(b, IPM) == -c;  // y -> -y flips the sign
+        Hs[tri(a, b)] = madd(Hs[tri(a, b)], xo ? (yo ? oo : oe) : (yo ? eo : ee), c);
+      }
+    }
   }
   __device__ __forceinline__ float F() const { return Fs; }
   __device__ __forceinline__ void scale(float z) {
