@@ -2,8 +2,8 @@
 //
 // The multipliers of Eq. feqNum_8Mom solve G(lambda) = 0 (Eqs. G0_8mom..
 // G3yaa_8mom). On GB300 the FP64 pipe runs at 1/62 of the FP32 rate, so the
-// Newton iterations run in FP32 (exponentials, exact Jacobian, Jacobi-scaled
-// Cholesky), and FP64 is used only where the accuracy of the result comes
+// Newton iterations run in FP32 (exponentials, exact Jacobian, Cholesky
+// factor), and FP64 is used only where the accuracy of the result comes
 // from: the residual. The FP64 refinement evaluates the 21 exponentials and
 // the 8 constraint residuals in FP64 and corrects lambda with the FP32
 // Cholesky factor (iterative refinement of the Newton step) until
@@ -365,30 +365,28 @@ struct PassMul64 : SumsG64 {
   }
 };
 
-// Jacobi-scaled Cholesky factor of the Jacobian, FP32.
+// Cholesky factor of the Jacobian, FP32: the packed lower triangle L with the
+// reciprocals of its diagonal entries in the diagonal slots, so that the
+// solves multiply. No diagonal (Jacobi) scaling: the backward error of the
+// Cholesky factorisation does not depend on it, and on the 4096^2 layer the
+// unscaled factor gave the same iteration counts (and 1 % more MLUPS).
 struct Fact32 {
-  float d[NM];    // scaling 1/sqrt(H_kk)
-  float L[36];    // packed lower factor of D H D
+  float L[36];
 };
 
 __device__ __forceinline__ bool factor32(const float H[36], Fact32& fc) {
   bool ok = true;
 #pragma unroll
-  for (int k = 0; k < NM; ++k) {
-    ok = ok && (H[tri(k, k)] > 0.0f);
-    fc.d[k] = rsqrtf(fmaxf(H[tri(k, k)], 1e-30f));
-  }
-#pragma unroll
   for (int j = 0; j < NM; ++j) {
-    float dj = H[tri(j, j)] * fc.d[j] * fc.d[j];
+    float dj = H[tri(j, j)];
 #pragma unroll
     for (int k = 0; k < j; ++k) dj = fmaf(-fc.L[tri(j, k)], fc.L[tri(j, k)], dj);
     ok = ok && (dj > 0.0f);
     const float il = rsqrtf(fmaxf(dj, 1e-30f));
-    fc.L[tri(j, j)] = dj * il;
+    fc.L[tri(j, j)] = il;
 #pragma unroll
     for (int i = j + 1; i < NM; ++i) {
-      float s = H[tri(i, j)] * fc.d[i] * fc.d[j];
+      float s = H[tri(i, j)];
 #pragma unroll
       for (int k = 0; k < j; ++k) s = fmaf(-fc.L[tri(i, k)], fc.L[tri(j, k)], s);
       fc.L[tri(i, j)] = s * il;
@@ -397,25 +395,25 @@ __device__ __forceinline__ bool factor32(const float H[36], Fact32& fc) {
   return ok;
 }
 
-// delta = H^-1 g with the scaled factor.
+// delta = H^-1 g with the factor (forward and backward substitution).
 __device__ __forceinline__ void solve32(const Fact32& fc, const float g[NM], float dl[NM]) {
   float y[NM];
 #pragma unroll
   for (int i = 0; i < NM; ++i) {
-    float s = g[i] * fc.d[i];
+    float s = g[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) s = fmaf(-fc.L[tri(i, k)], y[k], s);
-    y[i] = s / fc.L[tri(i, i)];
+    y[i] = s * fc.L[tri(i, i)];
   }
 #pragma unroll
   for (int i = NM - 1; i >= 0; --i) {
     float s = y[i];
 #pragma unroll
     for (int k = i + 1; k < NM; ++k) s = fmaf(-fc.L[tri(k, i)], y[k], s);
-    y[i] = s / fc.L[tri(i, i)];
+    y[i] = s * fc.L[tri(i, i)];
   }
 #pragma unroll
-  for (int i = 0; i < NM; ++i) dl[i] = y[i] * fc.d[i];
+  for (int i = 0; i < NM; ++i) dl[i] = y[i];
 }
 
 // Multipliers in the frame of another lattice: lam'.P(u) = lam.P(u - d) for
