@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1)
     dT[1] = 0.5 * (T1 - T2);
     const int U0x = select_shift(ux, pr.n0, pr.umax), U0y = select_shift(uy, pr.n0, pr.umax);
     const int code = lat_code(U0x, U0y);
-    double lam[NM];
+    P lam[NM];
     const bool realizable = (r > 0.0) && (T > 0.0) && isfinite(r) && isfinite(T);
     const int ns = realizable ? node_equilibrium<P>(pr, ux - U0x, uy - U0y, T, s_tab, nullptr,
                                                     cl.eq, lam, &cnt)
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(BLOCK, (std::is_same<P, float>::value ? 4 : 1)
       // flow starts its solves from previous multipliers
       P wbuf[NM];
 #pragma unroll
-      for (int j = 0; j < NM; ++j) wbuf[j] = (P)lam[j];
+      for (int j = 0; j < NM; ++j) wbuf[j] = lam[j];
       // with the neighbourhood rule, the neighbours' initial lattices (Eq.
       // criterion on their initial velocities, boundary rule outside the grid)
       uint8_t nb[8];
@@ -227,10 +227,15 @@ __global__ void __launch_bounds__(BLOCK)
   pr.maxit = maxit;
   SolveCount cnt;
   int st = NEWTON_UNREALIZABLE;
-  if (r > 0.0)
-    st = precision == 0
-             ? node_equilibrium<double>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, eq, lam, &cnt)
-             : node_equilibrium<float>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, eq, lam, &cnt);
+  if (r > 0.0) {
+    if (precision == 0) {
+      st = node_equilibrium<double>(pr, ubx[k], uby[k], T[k], s_tab, nullptr, eq, lam, &cnt);
+    } else {
+      float l32[NM];  // the FP64 multipliers are asked for here
+      st = equilibrium_mixed(ubx[k], uby[k], T[k], tol, maxit, s_tab, nullptr, eq, BLOCK, l32,
+                             lam, &cnt);
+    }
+  }
   for (int i = 0; i < Q; ++i) feq[(size_t)k * Q + i] = st == NEWTON_UNREALIZABLE ? 0.0 : r * eq[i * BLOCK];
   if (lambda)
 #pragma unroll

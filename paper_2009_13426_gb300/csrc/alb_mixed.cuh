@@ -582,15 +582,29 @@ __device__ __forceinline__ float step_exponent_bound(const float dl[NM]) {
 // column multiplicatively instead (PassMul64), else it evaluates them again.
 // On NEWTON_OK the FP64 equilibrium per unit density at the returned lambda
 // is in col[i * stride] (a shared-memory column of the calling thread).
-// *evals counts the full evaluations, *updates the multiplicative ones.
+// The residual is formed in FP64 and its maximum taken on its FP32 copy (the
+// one the correction is solved with; FP32 resolves 1e-12 to 6e-8 of itself).
+// The corrections are summed in FP32 for lam_out32 (lam32 plus every step:
+// the multipliers the warm start stores in FP32) and join the FP64
+// multipliers only before a full evaluation and, if lam_out64 is given, at
+// the end. *evals counts the full evaluations, *updates the multiplicative
+// ones.
 static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T, double tol,
                                                int maxr, const float lam32[NM], const Fact32& fc,
                                                const double* tab, double* col, int stride,
-                                               double lam[NM], int* evals, int* updates) {
+                                               float lam_out32[NM], double* lam_out64,
+                                               int* evals, int* updates) {
   double m[NM];
   targets(ubx, uby, T, m);
+  double lam[NM];  // FP64 multipliers of the last full evaluation
+  float acc[NM];   // corrections since then
 #pragma unroll
-  for (int k = 0; k < NM; ++k) lam[k] = (double)lam32[k];
+  for (int k = 0; k < NM; ++k) {
+    lam[k] = (double)lam32[k];
+    acc[k] = 0.0f;
+    lam_out32[k] = lam32[k];
+  }
+  const float tolf = (float)tol;
   *evals = 0;
   *updates = 0;
   float dl[NM];
@@ -604,27 +618,43 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
 #pragma unroll
       for (int k = 0; k < NM; ++k) M[k] = pu.M[k];
     } else {
+      if (r > 0) {
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+          lam[k] += (double)acc[k];
+          acc[k] = 0.0f;
+        }
+      }
       PassG64<true> ps(tab, col, stride);
       visit_groups<double>(lam, ps);
       ++*evals;
 #pragma unroll
       for (int k = 0; k < NM; ++k) M[k] = ps.M[k];
     }
-    double gmax = 0.0;
+    float gmax = 0.0f;
+    bool finite = true;
     float g32[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
-      const double G = M[k] - m[k];
-      gmax = fmax(gmax, fabs(G));
-      g32[k] = (float)G;
+      g32[k] = (float)(M[k] - m[k]);
+      finite = finite && isfinite(g32[k]);
+      gmax = fmaxf(gmax, fabsf(g32[k]));
     }
-    if (!isfinite(gmax)) return NEWTON_SINGULAR;
-    if (gmax <= tol) return NEWTON_OK;
+    if (!finite) return NEWTON_SINGULAR;
+    if (gmax <= tolf) {
+      if (lam_out64)
+#pragma unroll
+        for (int k = 0; k < NM; ++k) lam_out64[k] = lam[k] + (double)acc[k];
+      return NEWTON_OK;
+    }
     if (r >= maxr) return NEWTON_MAXIT;
     solve32(fc, g32, dl);
     small_step = step_exponent_bound(dl) <= 1e-3f;
 #pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] += (double)dl[k];
+    for (int k = 0; k < NM; ++k) {
+      acc[k] += dl[k];
+      lam_out32[k] += dl[k];
+    }
   }
 }
 
@@ -978,37 +1008,44 @@ static __device__ __noinline__ int newton4_fp64g(double ubx, double uby, double 
 // Equilibrium of the FP32 form: FP32 Newton (from the warm start if given,
 // else from the Maxwellian; again from the Maxwellian if the warm start
 // fails), FP64 refinement, full FP64 Newton as the last fallback. The FP64
-// equilibrium per unit density lands in col[i * stride].
+// equilibrium per unit density lands in col[i * stride]; the multipliers in
+// lam32 (FP32, as the warm start keeps them) and, if lam64 is given, in FP64.
 __device__ __forceinline__ int equilibrium_mixed(double ubx, double uby, double T, double tol,
                                                  int maxit, const double* tab, const float* warm,
-                                                 double* col, int stride, double lam[NM],
-                                                 SolveCount* cnt) {
+                                                 double* col, int stride, float lam32[NM],
+                                                 double* lam64, SolveCount* cnt) {
   if (!(T > 0.0) || !isfinite(T) || !isfinite(ubx) || !isfinite(uby)) return NEWTON_UNREALIZABLE;
-  float lam32[NM];
+  float l32[NM];
   Fact32 fc;
   int it32 = 0, ev = 0;
   int st = NEWTON_SINGULAR;
   if (warm) {
 #pragma unroll
-    for (int k = 0; k < NM; ++k) lam32[k] = warm[k];
-    st = newton_fp32((float)ubx, (float)uby, (float)T, 30, true, lam32, fc, &it32);
+    for (int k = 0; k < NM; ++k) l32[k] = warm[k];
+    st = newton_fp32((float)ubx, (float)uby, (float)T, 30, true, l32, fc, &it32);
     cnt->fp32_iters += it32;
   }
   if (st != NEWTON_OK) {
-    st = newton_fp32((float)ubx, (float)uby, (float)T, 30, false, lam32, fc, &it32);
+    st = newton_fp32((float)ubx, (float)uby, (float)T, 30, false, l32, fc, &it32);
     cnt->fp32_iters += it32;
   }
   if (st == NEWTON_OK) {
     int up = 0;
-    st = refine_fp64(ubx, uby, T, tol, 6, lam32, fc, tab, col, stride, lam, &ev, &up);
+    st = refine_fp64(ubx, uby, T, tol, 6, l32, fc, tab, col, stride, lam32, lam64, &ev, &up);
     cnt->fp64_evals += ev;
     cnt->fp64_updates += up;
   }
   if (st != NEWTON_OK) {
     int it = 0;
-    st = newton_fp64g(ubx, uby, T, tol, maxit, tab, col, stride, lam, &it, &ev, nullptr);
+    double ld[NM];
+    st = newton_fp64g(ubx, uby, T, tol, maxit, tab, col, stride, ld, &it, &ev, nullptr);
     cnt->fp64_iters += it;
     cnt->fp64_evals += ev;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      lam32[k] = (float)ld[k];
+      if (lam64) lam64[k] = ld[k];
+    }
   }
   return st;
 }

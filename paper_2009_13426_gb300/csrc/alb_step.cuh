@@ -36,31 +36,34 @@ struct Columns {
 // Equilibrium of one node in the storage precision P: the full FP64 Newton for
 // the FP64 plain path, the mixed FP32/FP64 solver for the FP32 form, both
 // started from `warm` (multipliers in precision P) when given. The
-// equilibrium per unit density lands in eq[i * B].
+// equilibrium per unit density lands in eq[i * B], the multipliers (in the
+// precision P the warm start keeps them in) in lam.
 template <typename P, int B = BLOCK>
 __device__ __forceinline__ int node_equilibrium(const Params& pr, double ubx, double uby,
                                                 double T, const double* tab, const P* warm,
-                                                double* eq, double lam[NM], SolveCount* cnt) {
+                                                double* eq, P lam[NM], SolveCount* cnt) {
   if (pr.moments == 4) {
     // reduced model: FP64 4x4 Newton in both precisions
-    double w8[NM];
+    double w8[NM], l8[NM];
     if (warm)
 #pragma unroll
       for (int k = 0; k < NM; ++k) w8[k] = (double)warm[k];
     int it = 0, ev = 0;
-    int st = newton4_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev,
+    int st = newton4_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, l8, &it, &ev,
                            warm ? w8 : nullptr);
     cnt->fp64_iters += it;
     cnt->fp64_evals += ev;
     if (warm && st != NEWTON_OK && st != NEWTON_UNREALIZABLE) {
-      st = newton4_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev, nullptr);
+      st = newton4_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, l8, &it, &ev, nullptr);
       cnt->fp64_iters += it;
       cnt->fp64_evals += ev;
     }
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = (P)l8[k];
     return st;
   }
   if constexpr (std::is_same<P, float>::value) {
-    return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, eq, B, lam, cnt);
+    return equilibrium_mixed(ubx, uby, T, pr.tol, pr.maxit, tab, warm, eq, B, lam, nullptr, cnt);
   } else {
     int it = 0, ev = 0;
     int st = newton_fp64g(ubx, uby, T, pr.tol, pr.maxit, tab, eq, B, lam, &it, &ev, warm);
@@ -153,7 +156,7 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   dT[0] = 0.5 * ((double)mT[kxp] - (double)mT[kxm]);
   dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
   const double ubx = ux - Upx, uby = uy - Upy;
-  double lam[NM];
+  P lam[NM];
   P wbuf[NM];
   const P* warm = nullptr;
   if (pr.warm) {
@@ -165,6 +168,7 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   const double gfac = (2.0 * pr.cv - 2.0) * T;
   if (st != NEWTON_OK) {
     if (T > 0.0) {
+      double lam[NM];
       maxwellian_guess(ubx, uby, T, lam);
       *fi = rho * exp_family_one(lam, cx, cy);
     } else {
@@ -307,14 +311,14 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
                                      select_shift_neighbours(uy, 1, nb, pr))
                           : lat_code(select_shift_kept(ux, Ux, pr), select_shift_kept(uy, Uy, pr));
 
-  double lam[NM];
+  P lam[NM];
   const int ns = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, cl.eq, lam, cnt)
                              : NEWTON_UNREALIZABLE;
   // multipliers for the next step's warm start (lattice `code`), if stored
   if (lam_out) {
     if (ns == NEWTON_OK) {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = (P)lam[j];
+      for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = lam[j];
     } else if (warm) {
 #pragma unroll
       for (int j = 0; j < NM; ++j) lam_out[j * ps + k] = warm[j];
