@@ -229,6 +229,7 @@ __device__ __forceinline__ void grad_phi(const Params& pr, double rho, double T,
 // Resolve a coordinate along one axis: periodic wrap or zero-gradient clamp.
 __device__ __forceinline__ int resolve(int x, int n, int bc, bool* ghost) {
   if (bc == 0) {
+    if ((unsigned)x < (unsigned)n) return x;  // inside: no remainder needed
     int r = x % n;
     if (r < 0) r += n;
     return r;

@@ -440,20 +440,42 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
     k = (size_t)y * pr.nx + x;
     code = a.nxt_in[k];
     const int Upx = lat_ux(code), Upy = lat_uy(code);
+    // Three passes, so that each kind of load is in flight for all 21
+    // velocities at once (a pull's load written straight to shared memory
+    // would wait for the previous velocity's): the senders' lattice codes,
+    // the populations of the senders in this node's lattice, then the
+    // shared-memory column and the queue of missing pulls.
+    size_t ks[Q];
+    unsigned own = 0;  // bit i: the sender of velocity i lives in lattice `code`
+    {
+      int sc[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        bool gh = false;
+        const int rx = resolve(x - XI_X(i) - Upx, pr.nx, pr.bcx, &gh);
+        const int ry = resolve(y - XI_Y(i) - Upy, pr.ny, pr.bcy, &gh);
+        ks[i] = (size_t)ry * pr.nx + rx;
+        sc[i] = gh ? -1 : (int)a.lat_in[ks[i]];  // a ghost sender is always rebuilt
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) own |= (sc[i] == code ? 1u : 0u) << i;
+    }
+    // populations are read once and written once per step: streaming
+    // (evict-first) loads and stores keep L2 for the lattice codes and the
+    // threads' stack
+    P v[2 * Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int sx = x - XI_X(i) - Upx;
-      const int sy = y - XI_Y(i) - Upy;
-      bool gh = false;
-      const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
-      const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
-      const size_t ks = (size_t)ry * pr.nx + rx;
-      if (!gh && a.lat_in[ks] == code) {
-        // populations are read once and written once per step: streaming
-        // (evict-first) loads and stores keep L2 for the lattice codes and
-        // the threads' stack
-        cl.pop[i * B] = __ldcs(&a.pop_in[i * ps + ks]);
-        cl.pop[(Q + i) * B] = __ldcs(&a.pop_in[(Q + i) * ps + ks]);
+      if (own & (1u << i)) {
+        v[i] = __ldcs(&a.pop_in[i * ps + ks[i]]);
+        v[Q + i] = __ldcs(&a.pop_in[(Q + i) * ps + ks[i]]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (own & (1u << i)) {
+        cl.pop[i * B] = v[i];
+        cl.pop[(Q + i) * B] = v[Q + i];
       } else {
         rq.entry[atomicAdd(&rq.count, 1)] = (unsigned short)((t << 5) | i);
       }
