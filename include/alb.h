@@ -297,8 +297,9 @@ int alb_equilibrium(const double* rho, const double* ubx, const double* uby, con
 int alb_exp_neg(const double* s, int n, double* out, void* stream);
 
 /* The same with the cheaper variant of the FP32 form's FP64 residual
- * evaluations: one-step reduction and degree-3 polynomial, relative error
- * below 2e-13. Same arguments and limits. */
+ * evaluations: table index from an FP32 copy of s, one-step reduction and
+ * degree-3 polynomial, relative error below 2e-13 for |s| <= 700. Same
+ * arguments and limits. */
 int alb_exp_neg_refine(const double* s, int n, double* out, void* stream);
 
 /* Shift criterion (Eq. criterion with offset n0, clamped to +-u_max) applied

@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # step kernel to the slots this model gives for the same launch; it absorbs
 # what the hand count misses (compiler scheduling, predication) and is
 # measured again whenever a kernel changes.
-CALIBRATION = {"fp32": 640.9 / 699.9, "fp64": 5573.7 / 6073.3}
+CALIBRATION = {"fp32": 576.3 / 565.5, "fp64": 5573.7 / 6073.3}
 
 BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
                   "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}
@@ -105,19 +105,21 @@ def plain_call():
 
 def mixed_eval():
     """FP64 residual evaluation of the refinement: grouped exponents (55),
-    21 table-driven exponentials (7 each: one-step reduction 3, degree-3
-    polynomial 3, scaling 1), grouped constraint sums (68), the residual and
-    its FP32 copy (16; its maximum is taken in FP32, and the FP32 corrections
-    join the FP64 multipliers only before a further full evaluation)."""
-    return 55 + 21 * 7 + 68 + 16
+    21 table-driven exponentials (6 each: the table index, taken from an FP32
+    copy of the exponent, converted to FP64, the one-step reduction, the
+    degree-3 polynomial 3, the scaling), grouped constraint sums started at
+    -m so that they end as the residual (68), its FP32 copy (8; its maximum
+    is taken in FP32, and the FP32 corrections join the FP64 multipliers only
+    before a further full evaluation)."""
+    return 55 + 21 * 6 + 68 + 8
 
 
 def mixed_update():
     """Multiplicative FP64 update of the refinement after a small step: per
     velocity the FP32 factor exp(-d) - 1 converted to FP64 and one FMA
-    (21 x 2; the exponent changes d are FP32), grouped constraint sums (68),
-    the residual and its FP32 copy (16)."""
-    return 21 * 2 + 68 + 16
+    (21 x 2; the exponent changes d are FP32), grouped constraint sums
+    started at -m (68), the residual's FP32 copy (8)."""
+    return 21 * 2 + 68 + 8
 
 
 def mixed_call():
@@ -126,11 +128,13 @@ def mixed_call():
 
 
 COLLISION = {
-    # moments from the sums (4 conversions, 3 divides, ~10 ops), criterion
-    # (~24), tau and 1/tau, equilibria rho p and g^eq with one conversion of
-    # each FP64 value to FP32 (63); the stored multipliers come out of the
+    # FP64 part only: the 4 FP32 sums converted, one reciprocal of rho and 8
+    # operations for u and T, the velocities in the absolute frame (4), the
+    # criterion's comparisons (8), the FP32 view of the equilibrium column (21
+    # conversions), T, rho and the stored moments in FP32 (6); tau, the
+    # sensor and BGK run in FP32, and the stored multipliers come out of the
     # solver in FP32
-    "fp32": 4 + 3 * W_DIV + 10 + 24 + 2 * W_DIV + 3 + 63,
+    "fp32": 4 + W_DIV + 8 + 4 + 8 + 21 + 6,
     "fp64": 90 + 3 * W_DIV + 5 + 2 + 24 + (W_DIV + 1) + W_DIV + 21 * 7 + 2,
 }
 
@@ -166,7 +170,7 @@ def method_floor(mlups: float) -> dict:
     constraint sums), the least a solve needs to confirm max|G|/rho <= 1e-12
     in FP64 (App. C.1). Returns that count, the MLUPS the FP64 pipe would
     allow if it were all the work, and the fraction of it `mlups` reaches."""
-    slots = 55 + 21 * 7 + 68
+    slots = 55 + 21 * 6 + 68
     cap = FP64_PEAK_TFLOPS * 1e12 / 2.0 / slots / 1e6
     return {"fp64_slots_per_node": slots, "mlups_at_fp64_peak": round(cap, 1),
             "frac": round(mlups / cap, 4)}

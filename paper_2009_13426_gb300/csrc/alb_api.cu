@@ -206,6 +206,7 @@ int alb_create(const alb_config* cfg, alb_handle** out) {
   p.tol = cfg->newton_tol;
   p.cv = 1.0 / (cfg->gamma - 1.0);
   p.cp = cfg->gamma * p.cv;
+  p.half_gm1 = 0.5 * (cfg->gamma - 1.0);
   p.shakhov = cfg->prandtl != 1.0 ? 1 : 0;
   p.prandtl = cfg->prandtl;
   for (int j = 0; j < 3; ++j) {

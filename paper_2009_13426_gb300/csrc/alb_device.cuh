@@ -57,6 +57,7 @@ struct Params {
   double prandtl;    // Pr: tau_Pr = 1/2 + (nu/Pr)/T, kappa = rho Cp nu / Pr
   double overlap;    // widening of the current shift's range (0: Eq. criterion)
   double cv, cp;     // Cv = 1/(gamma-1), Cp = gamma Cv
+  double half_gm1;   // (gamma - 1) / 2 = 1 / (2 Cv)
   double seps[3], salpha[3];
   double skx[4], sky[4];  // sensor knots: log10(eps) and alpha (host-computed)
   double thr[6];          // criterion thresholds (t + 1) - n0, t = -umax .. umax - 1

@@ -250,7 +250,7 @@ __global__ void exp_neg_kernel(const double* s, int n, double* out) {
   __shared__ double s_tab[EXPT_N];
   load_exptab(s_tab);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) out[k] = REFINE ? exp_neg_refine(s[k], s_tab) : exp_neg(s[k], s_tab);
+  if (k < n) out[k] = REFINE ? exp_neg_refine(s[k], (float)s[k], s_tab) : exp_neg(s[k], s_tab);
 }
 
 __global__ void select_kernel(const double* rho, const double* rhou, int n, double n0, int umax,

@@ -23,6 +23,8 @@
 // formed once for all moments).
 #pragma once
 
+#include <type_traits>
+
 #include "alb_device.cuh"
 #include "exp_table.h"
 
@@ -128,23 +130,48 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
 // relative accuracy only (their tolerance is 1e-12 on G/rho and the result is
 // rounded to FP32): the same table, the reduction in one step with ln2/N
 // rounded, and the degree-3 Taylor polynomial (truncation below 1.4e-13).
-// 7 FP64 operations.
-__device__ __forceinline__ double exp_neg_refine(double s, const double* tab) {
-  const double shifter = 6755399441055744.0;
-  const double t = fma(-s, EXPT_INV_L, shifter);
-  const int n = (int)(unsigned)__double2loint(t);
-  const double nd = t - shifter;
-  const double r = fma(nd, -EXPT_L, -s);
+// The table index n nearest to -s N / ln2 comes from s32, an FP32 value of
+// the same exponent: within |s| <= 745 (past which the result is 0 or +inf
+// anyway) FP32 holds s to 5e-5, a fiftieth of ln2/N, so n is the nearest
+// integer or its neighbour at a tie and |r| stays below 0.52 ln2/N
+// (truncation below 1.6e-13). 6 FP64 operations: n converted to FP64, the
+// reduction, the polynomial and the scaling. For |s32 N / ln2| >= 2^31 the
+// conversion saturates and e takes the limits; a NaN gives n = 0 and passes
+// through the polynomial.
+__device__ __forceinline__ double exp_neg_refine(double s, float s32, const double* tab) {
+  const int n = __float2int_rn(-s32 * (float)EXPT_INV_L);
+  const double r = fma((double)n, -EXPT_L, -s);
   double q = fma(r, EXPT_C3, EXPT_C2);
   q = fma(q, r, 1.0);
   q = fma(q, r, 1.0);
-  const int e = exp_scale_exponent(t, n);
-  const long long bits =
-      __double_as_longlong(tab[n & (EXPT_N - 1)]) + ((long long)e << 52);
+  const int e = n >> EXPT_BITS;
+  const int ec = e < -1100 ? -1100 : (e > 1100 ? 1100 : e);  // keeps the shift defined
+  const long long bits = __double_as_longlong(tab[n & (EXPT_N - 1)]) + ((long long)ec << 52);
   const double v = q * __longlong_as_double(bits);
   // out of range: the limits themselves (q need not be finite there)
   return e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : v);
 }
+
+// An exponent held twice: in FP64 and in FP32 (the FP32 copy picks the
+// table index of exp_neg_refine). visit_groups runs on it unchanged; its
+// operators live in a namespace of their own, found by argument-dependent
+// lookup, so that they hide no FP64 fma.
+namespace dual {
+struct Exp2 {
+  double d;
+  float f;
+  Exp2() = default;
+  __device__ __forceinline__ Exp2(double d_, float f_) : d(d_), f(f_) {}
+  __device__ __forceinline__ explicit Exp2(double c) : d(c), f((float)c) {}
+};
+__device__ __forceinline__ Exp2 operator+(Exp2 a, Exp2 b) { return Exp2(a.d + b.d, a.f + b.f); }
+__device__ __forceinline__ Exp2 operator-(Exp2 a, Exp2 b) { return Exp2(a.d - b.d, a.f - b.f); }
+__device__ __forceinline__ Exp2 operator*(Exp2 a, Exp2 b) { return Exp2(a.d * b.d, a.f * b.f); }
+__device__ __forceinline__ Exp2 fma(Exp2 a, Exp2 b, Exp2 c) {
+  return Exp2(::fma(a.d, b.d, c.d), fmaf(a.f, b.f, c.f));
+}
+}  // namespace dual
+using dual::Exp2;
 
 // Packed lower triangle of the 8x8 Jacobian: entry (a, b), b <= a.
 __host__ __device__ constexpr int tri(int a, int b) { return a * (a + 1) / 2 + b; }
@@ -238,9 +265,11 @@ struct PassGH32 {
 // difference, a diagonal quadruple through its four parity combinations.
 struct SumsG64 {
   double M[NM];
-  __device__ __forceinline__ SumsG64() {
+  // The sums start at -m (the targets), so that they end as the residual
+  // G = sum p P - m without a separate subtraction.
+  __device__ __forceinline__ explicit SumsG64(const double m[NM]) {
 #pragma unroll
-    for (int k = 0; k < NM; ++k) M[k] = 0.0;
+    for (int k = 0; k < NM; ++k) M[k] = -m[k];
   }
   __device__ __forceinline__ void add_rest(double p) { M[0] += p; }
   template <int A, int AX>
@@ -286,16 +315,23 @@ struct PassG64 {
 #pragma unroll
     for (int k = 0; k < NM; ++k) M[k] = 0.0;
   }
-  __device__ __forceinline__ double ex(double s) const {
-    return REFINE ? exp_neg_refine(s, tab) : exp_neg(s, tab);
+  // sums started at -m: they end as the residual G = sum p P - m
+  __device__ __forceinline__ PassG64(const double* t, double* c, int s, const double m[NM])
+      : tab(t), col(c), stride(s) {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) M[k] = -m[k];
   }
-  __device__ __forceinline__ void rest(double s) {
+  // exponents: double, or Exp2 (FP64 with an FP32 copy) in the refinement
+  using S = typename std::conditional<REFINE, Exp2, double>::type;
+  __device__ __forceinline__ double ex(double s) const { return exp_neg(s, tab); }
+  __device__ __forceinline__ double ex(Exp2 s) const { return exp_neg_refine(s.d, s.f, tab); }
+  __device__ __forceinline__ void rest(S s) {
     const double p = ex(s);
     col[0] = p;
     M[0] += p;
   }
   template <int A, int AX, int IP, int IM>
-  __device__ __forceinline__ void pair(double sp, double sm) {
+  __device__ __forceinline__ void pair(S sp, S sm) {
     const double pp = ex(sp), pm = ex(sm);
     col[IP * stride] = pp;
     col[IM * stride] = pm;
@@ -312,7 +348,7 @@ struct PassG64 {
     }
   }
   template <int A, int IPP, int IMP, int IMM, int IPM>
-  __device__ __forceinline__ void quad(double spp, double smp, double smm, double spm) {
+  __device__ __forceinline__ void quad(S spp, S smp, S smm, S spm) {
     const double ppp = ex(spp), pmp = ex(smp);
     const double pmm = ex(smm), ppm = ex(spm);
     col[IPP * stride] = ppp;
@@ -346,7 +382,8 @@ struct PassG64 {
 struct PassMul64 : SumsG64 {
   double* col;
   int stride;
-  __device__ __forceinline__ PassMul64(double* c, int s) : col(c), stride(s) {}
+  __device__ __forceinline__ PassMul64(double* c, int s, const double m[NM])
+      : SumsG64(m), col(c), stride(s) {}
   __device__ __forceinline__ double upd(int i, float d) const {
     const float e = d * fmaf(d, fmaf(d, -1.0f / 6.0f, 0.5f), -1.0f);
     double* q = col + (size_t)i * stride;
@@ -610,13 +647,13 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
   float dl[NM];
   bool small_step = false;
   for (int r = 0;; ++r) {
-    double M[NM];
+    double G[NM];  // residual sum p P - m
     if (small_step) {
-      PassMul64 pu(col, stride);
+      PassMul64 pu(col, stride, m);
       visit_groups<float>(dl, pu, 0.0f);
       ++*updates;
 #pragma unroll
-      for (int k = 0; k < NM; ++k) M[k] = pu.M[k];
+      for (int k = 0; k < NM; ++k) G[k] = pu.M[k];
     } else {
       if (r > 0) {
 #pragma unroll
@@ -625,18 +662,21 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
           acc[k] = 0.0f;
         }
       }
-      PassG64<true> ps(tab, col, stride);
-      visit_groups<double>(lam, ps);
+      PassG64<true> ps(tab, col, stride, m);
+      Exp2 l2[NM];
+#pragma unroll
+      for (int k = 0; k < NM; ++k) l2[k] = Exp2(lam[k], lam_out32[k]);
+      visit_groups<Exp2>(l2, ps, Exp2(1.0));
       ++*evals;
 #pragma unroll
-      for (int k = 0; k < NM; ++k) M[k] = ps.M[k];
+      for (int k = 0; k < NM; ++k) G[k] = ps.M[k];
     }
     float gmax = 0.0f;
     bool finite = true;
     float g32[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
-      g32[k] = (float)(M[k] - m[k]);
+      g32[k] = (float)G[k];
       finite = finite && isfinite(g32[k]);
       gmax = fmaxf(gmax, fabsf(g32[k]));
     }

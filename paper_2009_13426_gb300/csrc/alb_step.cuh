@@ -301,8 +301,19 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   // that the collision conserves the sums to their own precision; the next
   // lattice (Eq. criterion) is chosen from u = (rho u) / rho in FP64.
   const double rho = ar.val();
-  const double ubx = ajx.val() / rho, uby = ajy.val() / rho;
-  const double T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
+  double ubx, uby, T;
+  if constexpr (std::is_same<P, float>::value) {
+    // FP32 sums: one FP64 reciprocal serves the three quotients (their last
+    // FP64 bit lies far below the sums' own precision); 1/(2 Cv) = (gamma-1)/2
+    const double ir = 1.0 / rho;
+    ubx = ajx.val() * ir;
+    uby = ajy.val() * ir;
+    T = (ae.val() - rho * (ubx * ubx + uby * uby)) * ir * pr.half_gm1;
+  } else {
+    ubx = ajx.val() / rho;
+    uby = ajy.val() / rho;
+    T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
+  }
   const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
   // next lattice: Eq. criterion, or overlapping ranges chosen by history or
   // by the neighbours' current lattices nb[0..7]
