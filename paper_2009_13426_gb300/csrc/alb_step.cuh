@@ -125,13 +125,17 @@ __device__ __forceinline__ void load_warm(const L* lam, size_t ps, size_t k, int
 // h* = h^eq (1 + (1 - 1/tau) phi_h), plus (1/tau - 1/tau_Pr) h^eq phi_h,q for
 // Pr != 1 (the collision of App. E applied to the Grad population). Uses the
 // thread's equilibrium column as scratch. Returns 1 if the root finder failed
-// and the Maxwellian-guess fallback was used.
+// and the Maxwellian-guess fallback was used. With eq_led given, the
+// equilibrium of this sender in this lattice has been solved already (by
+// another pull of the block): its column eq_led and whether that solve
+// failed (led_failed) take the place of the solve.
 template <typename P, int B>
 __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ mom, size_t ps,
                                          int i, int cx, int cy, int Upx, int Upy, int sx, int sy,
                                          double* fi, double* gi, const double* tab, double* eq,
                                          const P* lam_in, const uint8_t* lat_in,
-                                         SolveCount* cnt) {
+                                         SolveCount* cnt, const double* eq_led = nullptr,
+                                         int led_failed = 0) {
   bool gh = false;
   const int rx = resolve(sx, pr.nx, pr.bcx, &gh);
   const int ry = resolve(sy, pr.ny, pr.bcy, &gh);
@@ -156,15 +160,21 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
   dT[0] = 0.5 * ((double)mT[kxp] - (double)mT[kxm]);
   dT[1] = 0.5 * ((double)mT[kyp] - (double)mT[kym]);
   const double ubx = ux - Upx, uby = uy - Upy;
-  P lam[NM];
-  P wbuf[NM];
-  const P* warm = nullptr;
-  if (pr.warm) {
-    load_warm<P>(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
-    warm = wbuf;
+  int st;
+  if (eq_led) {
+    st = led_failed ? NEWTON_MAXIT : NEWTON_OK;
+    eq = const_cast<double*>(eq_led);  // read only below
+  } else {
+    P lam[NM];
+    P wbuf[NM];
+    const P* warm = nullptr;
+    if (pr.warm) {
+      load_warm<P>(lam_in, ps, ks, lat_in[ks], Upx, Upy, wbuf);
+      warm = wbuf;
+    }
+    st = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, eq, lam, cnt)
+                     : NEWTON_UNREALIZABLE;
   }
-  const int st = (rho > 0.0) ? node_equilibrium<P, B>(pr, ubx, uby, T, tab, warm, eq, lam, cnt)
-                             : NEWTON_UNREALIZABLE;
   const double gfac = (2.0 * pr.cv - 2.0) * T;
   if (st != NEWTON_OK) {
     if (T > 0.0) {
@@ -423,6 +433,11 @@ __device__ __forceinline__ void flush_counts(unsigned long long* ctr, const Node
 template <int B>
 struct RebuildQueue {
   unsigned short entry[Q * B];
+  unsigned key[B];             // (receiver lattice, sender position in the tile's frame)
+  unsigned char failed[B];     // the entry's own solve fell back
+  unsigned short slot[B];      // leader entry solved by thread j
+  unsigned short solver[B];    // thread solving a leader entry
+  int wsum[B / 32];            // missing pulls per warp
   int count;
 };
 
@@ -447,6 +462,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
   const bool active = x < pr.nx && y < pr.ny;
   size_t k = 0;
   int code = 0;
+  unsigned own = 0;  // bit i: the sender of velocity i lives in lattice `code`
   if (active) {
     k = (size_t)y * pr.nx + x;
     code = a.nxt_in[k];
@@ -457,7 +473,6 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
     // the populations of the senders in this node's lattice, then the
     // shared-memory column and the queue of missing pulls.
     size_t ks[Q];
-    unsigned own = 0;  // bit i: the sender of velocity i lives in lattice `code`
     {
       int sc[Q];
 #pragma unroll
@@ -487,31 +502,115 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
       if (own & (1u << i)) {
         cl.pop[i * B] = v[i];
         cl.pop[(Q + i) * B] = v[Q + i];
-      } else {
-        rq.entry[atomicAdd(&rq.count, 1)] = (unsigned short)((t << 5) | i);
       }
     }
+  }
+  // The queue of missing pulls in (thread, velocity) order, placed by a
+  // block-wide prefix sum of the threads' counts, so that its order, and with
+  // it which pulls share a solve below, does not depend on scheduling.
+  {
+    const unsigned miss = active ? (~own & ((1u << Q) - 1u)) : 0u;
+    const int nmiss = __popc(miss), lane = t & 31, warp = t >> 5;
+    int incl = nmiss;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += u;
+    }
+    if (lane == 31) rq.wsum[warp] = incl;
+    __syncthreads();
+    int pos = incl - nmiss;
+    for (int w = 0; w < warp; ++w) pos += rq.wsum[w];
+    for (unsigned m = miss; m; m &= m - 1) rq.entry[pos++] = (unsigned short)((t << 5) | (__ffs(m) - 1));
+    if (t == B - 1) rq.count = pos;  // the last thread's end: the total
   }
   __syncthreads();
   const int nq = rq.count;
   P* pop0 = cl.pop - t;  // column 0 of the block
-  for (int e = t; e < nq; e += B) {
-    const int owner = rq.entry[e] >> 5, i = rq.entry[e] & 31;
-    const int ox = x0 + (owner & mask), oy = y0 + (owner >> lg);
-    const int ocode = a.nxt_in[(size_t)oy * pr.nx + ox];
-    const int Upx = lat_ux(ocode), Upy = lat_uy(ocode);
-    const int cx = XI_X(i), cy = XI_Y(i);
-    double fd, gd;
-    nc.rec += 1;
-    nc.calls += 1;
-    nc.rec_fail += rebuild_pull<P, B>(pr, a.mom_in, ps, i, cx, cy, Upx, Upy, ox - cx - Upx,
-                                      oy - cy - Upy, &fd, &gd, s_tab, cl.eq, a.lam_in, a.lat_in,
-                                      &nc.solve);
-    pop0[i * B + owner] = (P)fd;
-    pop0[(Q + i) * B + owner] = (P)gd;
+  // Entries in chunks of B. The pulls of one sender in one receiver lattice
+  // need the same equilibrium (the sender's state in that lattice, from the
+  // same warm start). Within a chunk, the first entry of each such group (its
+  // leader) is solved, by threads 0, 1, ... in entry order, so that the solves
+  // fill as few warps as possible; every other entry then reads its leader's
+  // column after a barrier. A solve's result does not depend on the thread,
+  // so sharing it changes no value.
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll 1
+  for (int base = 0; base < nq; base += B) {
+    const int ne = min(nq - base, B);
+    if (t < ne) {
+      const int owner = rq.entry[base + t] >> 5, i = rq.entry[base + t] & 31;
+      const int ox = x0 + (owner & mask), oy = y0 + (owner >> lg);
+      const int ocode = a.nxt_in[(size_t)oy * pr.nx + ox];
+      // the sender lies within 6 nodes of the tile (|xi| <= 3, |U| <= 3) and
+      // the tile's sides are at most B <= 1000: 10 bits per coordinate
+      const int sx = ox - XI_X(i) - lat_ux(ocode) - x0 + 8;
+      const int sy = oy - XI_Y(i) - lat_uy(ocode) - y0 + 8;
+      rq.key[t] = ((unsigned)ocode << 20) | ((unsigned)sy << 10) | (unsigned)sx;
+    }
+    __syncthreads();
+    int lead = -1;
+    if (t < ne) {
+      const unsigned key = rq.key[t];
+      lead = t;
+      for (int e = 0; e < t; ++e)
+        if (rq.key[e] == key) {
+          lead = e;
+          break;
+        }
+    }
+    // number the leaders (block-wide prefix sum of the leader flags)
+    const int isl = (t < ne && lead == t) ? 1 : 0;
+    int incl = isl;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += u;
+    }
+    if (lane == 31) rq.wsum[warp] = incl;
+    __syncthreads();
+    int nlead = 0, rank = incl - isl;
+    for (int w = 0; w < B / 32; ++w) {
+      nlead += rq.wsum[w];
+      if (w < warp) rank += rq.wsum[w];
+    }
+    if (isl) {
+      rq.slot[rank] = (unsigned short)t;    // solver thread rank -> leader entry
+      rq.solver[t] = (unsigned short)rank;  // leader entry -> its solver thread
+    }
+    __syncthreads();
+    // pass 0: thread j < nlead solves the j-th leader entry; pass 1: every
+    // other entry, with its leader's column
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass) __syncthreads();
+      const int e = pass == 0 ? (t < nlead ? (int)rq.slot[t] : -1)
+                              : (t < ne && lead != t ? t : -1);
+      if (e >= 0) {
+        const int owner = rq.entry[base + e] >> 5, i = rq.entry[base + e] & 31;
+        const int ox = x0 + (owner & mask), oy = y0 + (owner >> lg);
+        const int ocode = a.nxt_in[(size_t)oy * pr.nx + ox];
+        const int Upx = lat_ux(ocode), Upy = lat_uy(ocode);
+        const int cx = XI_X(i), cy = XI_Y(i);
+        const int j = pass ? (int)rq.solver[lead] : t;  // thread whose column holds the solve
+        double fd, gd;
+        const int failed = rebuild_pull<P, B>(
+            pr, a.mom_in, ps, i, cx, cy, Upx, Upy, ox - cx - Upx, oy - cy - Upy, &fd, &gd, s_tab,
+            cl.eq, a.lam_in, a.lat_in, &nc.solve, pass ? cl.eq - t + j : nullptr,
+            pass ? rq.failed[lead] : 0);
+        if (!pass) {
+          rq.failed[e] = (unsigned char)failed;
+          nc.calls += 1;
+        }
+        nc.rec += 1;
+        nc.rec_fail += failed;
+        pop0[i * B + owner] = (P)fd;
+        pop0[(Q + i) * B + owner] = (P)gd;
+      }
+    }
+    __syncthreads();  // the columns, keys and slots are reused by the next chunk
   }
   __syncthreads();
-  if (t == 0) rq.count = 0;  // ordered before the next use by the caller's barrier
   if (active) {
     const int Upx = lat_ux(code), Upy = lat_uy(code);
     P wbuf[NM];

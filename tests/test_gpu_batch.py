@@ -42,6 +42,17 @@ def state(fl):
     return fl.moments(), fl.shifts()
 
 
+# Work counters of the equilibrium solves depend on the tile shape: the
+# rebuilt pulls of one sender in one receiver lattice share a solve within a
+# tile. The state and the per-node and per-pull counters do not.
+SOLVE_WORK = ("newton_calls", "newton_iterations", "fp64_evaluations", "fp32_iterations",
+              "fp64_updates")
+
+
+def per_pull(st):
+    return {k: v for k, v in st.items() if k not in SOLVE_WORK}
+
+
 def alone(alb, sp, steps):
     fl = alb.Flow(**cfg_of(alb, sp))
     assert fl.init(*sp.fields()) == alb.ALB_OK
@@ -79,7 +90,7 @@ def test_batch_equals_alone_bit_for_bit(alb, reference):
         for k, fl in enumerate(b.flows):
             assert_same(state(fl), reference[k][STEPS][0], "flow %d" % k)
             st, ref = fl.stats(), reference[k][STEPS][1]
-            assert st == ref, (k, st, ref)
+            assert per_pull(st) == per_pull(ref), (k, st, ref)
     finally:
         b.close()
 
@@ -201,8 +212,9 @@ def _sync_flagged(alb, obj):
 def test_mixed_configurations_in_one_batch(alb):
     """Flows that differ in every per-flow option - overlap rules, sensor,
     zero-gradient ends, the reduced model, Maxwellian or previous starts, u_max,
-    n0 - share one launch and each stays bit-identical to its own run,
-    counters (including any flagged rebuild failures) included."""
+    n0 - share one launch and each stays bit-identical to its own run, its
+    per-node and per-pull counters (including any flagged rebuild failures)
+    included."""
     ZG = alb.ALB_ZERO_GRADIENT
     specs = [
         (SPECS[0], dict(shift_overlap=0.5, shift_rule=alb.ALB_RULE_HISTORY)),
@@ -231,12 +243,6 @@ def test_mixed_configurations_in_one_batch(alb):
         for k, fl in enumerate(b.flows):
             assert_same(state(fl), ref[k][0], "flow %d" % k)
             got, want = fl.stats(), ref[k][1]
-            if want["reconstruction_failures"] or want["newton_failures"]:
-                # a failing root finder's discarded path: the two kernels are
-                # compiled apart and may fuse its multiply-adds differently
-                for key in ("newton_iterations", "fp64_evaluations"):
-                    got.pop(key)
-                    want.pop(key)
-            assert got == want, k
+            assert per_pull(got) == per_pull(want), k
     finally:
         b.close()
