@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # step kernel to the slots this model gives for the same launch; it absorbs
 # what the hand count misses (compiler scheduling, predication) and is
 # measured again whenever a kernel changes.
-CALIBRATION = {"fp32": 576.3 / 565.5, "fp64": 5573.7 / 6073.3}
+CALIBRATION = {"fp32": 554.4 / 526.7, "fp64": 5573.7 / 6073.3}
 
 BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
                   "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}

@@ -449,7 +449,7 @@ struct RebuildQueue {
 // solve, so spreading them keeps the warps of interface nodes from waiting on
 // a few lanes); phase 3 collides and stores. A rebuilt value depends only on
 // its inputs, not on the thread that computes it. All threads of the block
-// must call this (it holds two barriers).
+// must call this (it holds barriers).
 template <typename P, int B>
 __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, int lg,
                                           const Columns<P, B>& cl, const double* s_tab,
@@ -507,7 +507,9 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
   }
   // The queue of missing pulls in (thread, velocity) order, placed by a
   // block-wide prefix sum of the threads' counts, so that its order, and with
-  // it which pulls share a solve below, does not depend on scheduling.
+  // it which pulls share a solve below, does not depend on scheduling. A tile
+  // without missing pulls passes one barrier and skips the rest.
+  int nq = 0;
   {
     const unsigned miss = active ? (~own & ((1u << Q) - 1u)) : 0u;
     const int nmiss = __popc(miss), lane = t & 31, warp = t >> 5;
@@ -518,14 +520,16 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
       if (lane >= d) incl += u;
     }
     if (lane == 31) rq.wsum[warp] = incl;
-    __syncthreads();
-    int pos = incl - nmiss;
-    for (int w = 0; w < warp; ++w) pos += rq.wsum[w];
-    for (unsigned m = miss; m; m &= m - 1) rq.entry[pos++] = (unsigned short)((t << 5) | (__ffs(m) - 1));
-    if (t == B - 1) rq.count = pos;  // the last thread's end: the total
+    if (__syncthreads_or(nmiss)) {
+      int pos = incl - nmiss;
+      for (int w = 0; w < warp; ++w) pos += rq.wsum[w];
+      for (unsigned m = miss; m; m &= m - 1)
+        rq.entry[pos++] = (unsigned short)((t << 5) | (__ffs(m) - 1));
+      if (t == B - 1) rq.count = pos;  // the last thread's end: the total
+      __syncthreads();
+      nq = rq.count;
+    }
   }
-  __syncthreads();
-  const int nq = rq.count;
   P* pop0 = cl.pop - t;  // column 0 of the block
   // Entries in chunks of B. The pulls of one sender in one receiver lattice
   // need the same equilibrium (the sender's state in that lattice, from the
@@ -608,9 +612,10 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
         pop0[(Q + i) * B + owner] = (P)gd;
       }
     }
-    __syncthreads();  // the columns, keys and slots are reused by the next chunk
+    // the next chunk reuses the columns, keys and slots; the last chunk's
+    // rebuilt pulls are in place before the collisions
+    __syncthreads();
   }
-  __syncthreads();
   if (active) {
     const int Upx = lat_ux(code), Upy = lat_uy(code);
     P wbuf[NM];
