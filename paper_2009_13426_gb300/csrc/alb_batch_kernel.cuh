@@ -26,7 +26,6 @@ __global__ void __launch_bounds__(B, MINB)
   __shared__ __align__(16) unsigned long long s_args[sizeof(StepArgs<P>) / 8];
   __shared__ int s_item;
   __shared__ RebuildQueue<B> s_rq;
-  if (threadIdx.x == 0) s_rq.count = 0;
   load_exptab(s_tab);  // includes a barrier
   const StepArgs<P>& a = *reinterpret_cast<const StepArgs<P>*>(s_args);
   const Columns<P, B> cl(smem_raw);

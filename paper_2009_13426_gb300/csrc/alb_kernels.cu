@@ -45,7 +45,6 @@ __global__ void __launch_bounds__(StepShape<P>::B, StepShape<P>::MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_tab[EXPT_N];
   __shared__ RebuildQueue<B> s_rq;
-  if (threadIdx.x == 0) s_rq.count = 0;
   load_exptab(s_tab);  // includes a barrier
   const Columns<P, B> cl(smem_raw);
   NodeCount nc;
