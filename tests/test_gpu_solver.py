@@ -138,6 +138,13 @@ def test_refinement_exponential_within_its_bound(alb):
     assert rel.max() <= 2e-13, rel.max()
     assert rel.max() > 4 * 2.0 ** -52  # it is the cheaper variant
     _check_limits(alb.alb_exp_neg_refine)
+    # a NaN exponent (its FP32 copy converts to table index 0) stays NaN
+    t = _dev(np.array([np.nan, 1.0]))
+    o = torch.empty(2, dtype=torch.float64, device="cuda")
+    alb.alb_exp_neg_refine(t, 2, o)
+    torch.cuda.synchronize()
+    o = o.cpu().numpy()
+    assert np.isnan(o[0]) and abs(o[1] - np.exp(-1.0)) <= 2e-13 * np.exp(-1.0), o
 
 
 def test_refinement_keeps_the_exponential_form(alb):
