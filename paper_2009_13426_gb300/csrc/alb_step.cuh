@@ -538,6 +538,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
   // fill as few warps as possible; every other entry then reads its leader's
   // column after a barrier. A solve's result does not depend on the thread,
   // so sharing it changes no value.
+  static_assert(B % 32 == 0 && B <= 1000, "whole warps; tile sides fit the keys' 10-bit fields");
   const int lane = t & 31, warp = t >> 5;
 #pragma unroll 1
   for (int base = 0; base < nq; base += B) {
