@@ -64,13 +64,35 @@ struct Params {
   double wlo[7], whi[7];  // widened range of shift n = j - 3: ((n - n0) - w, ((n + 1) - n0) + w]
 };
 
+// Comparisons of the criterion on the integer pipe: the FP64 pipe bounds the
+// step, and an FP64 compare takes one of its slots. order_key maps a double's
+// bits to a signed integer in IEEE order (negative values have their
+// magnitude bits flipped). Integer order then equals IEEE order for all
+// non-NaN values except +0 against -0, which cannot meet here: the host's
+// thresholds are differences of distinct values, never -0, and a velocity
+// ubar + U with an integer U is never -0. A NaN u compares false both ways,
+// as in IEEE.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool not_nan(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool gt_order(double u, double v) {  // u > v
+  return not_nan(u) && order_key(u) > order_key(v);
+}
+__device__ __forceinline__ bool le_order(double u, double v) {  // u <= v
+  return not_nan(u) && order_key(u) <= order_key(v);
+}
+
 // Eq. criterion with the host-computed thresholds of Params (the same IEEE
 // values as select_shift computes).
 __device__ __forceinline__ int select_shift_thr(double u, const Params& pr) {
   int n = -pr.umax;
 #pragma unroll
   for (int t = 0; t < 6; ++t)
-    if (t < 2 * pr.umax && u > pr.thr[t]) ++n;
+    if (t < 2 * pr.umax && gt_order(u, pr.thr[t])) ++n;
   return n;
 }
 
@@ -78,7 +100,9 @@ __device__ __forceinline__ int select_shift_thr(double u, const Params& pr) {
 // while current - n0 - w < u <= current + 1 - n0 + w, else Eq. criterion.
 // The widened bounds come from the host (same IEEE operations as the oracle).
 __device__ __forceinline__ int select_shift_kept(double u, int current, const Params& pr) {
-  if (pr.overlap > 0.0 && pr.wlo[current + 3] < u && u <= pr.whi[current + 3]) return current;
+  if (order_key(pr.overlap) > 0 && gt_order(u, pr.wlo[current + 3]) &&
+      le_order(u, pr.whi[current + 3]))
+    return current;
   return select_shift_thr(u, pr);
 }
 
@@ -98,7 +122,7 @@ __device__ __forceinline__ int select_shift_neighbours(double u, int axis, const
   for (int d = -1; d <= 1; d += 2) {
     const int n = c + d;
     if (n < -pr.umax || n > pr.umax) continue;
-    if (!(pr.wlo[n + 3] < u && u <= pr.whi[n + 3])) continue;
+    if (!(gt_order(u, pr.wlo[n + 3]) && le_order(u, pr.whi[n + 3]))) continue;
     if (cnt[n + 3] > best_count) {
       best = n;
       best_count = cnt[n + 3];

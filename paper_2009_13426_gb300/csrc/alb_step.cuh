@@ -327,7 +327,7 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
   // next lattice: Eq. criterion, or overlapping ranges chosen by history or
   // by the neighbours' current lattices nb[0..7]
-  const bool by_nb = pr.overlap > 0.0 && pr.rule == 1 && nb;
+  const bool by_nb = order_key(pr.overlap) > 0 && pr.rule == 1 && nb;
   const int code2 = by_nb ? lat_code(select_shift_neighbours(ux, 0, nb, pr),
                                      select_shift_neighbours(uy, 1, nb, pr))
                           : lat_code(select_shift_kept(ux, Ux, pr), select_shift_kept(uy, Uy, pr));
@@ -626,7 +626,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
       warm = wbuf;
     }
     uint8_t nb[8];
-    if (pr.overlap > 0.0 && pr.rule == 1) neighbour_codes(pr, a.nxt_in, x, y, nb);
+    if (order_key(pr.overlap) > 0 && pr.rule == 1) neighbour_codes(pr, a.nxt_in, x, y, nb);
     collide_store<P, B>(pr, cl, code, k, ps, a.pop_out, a.mom_out, a.lat_out, a.nxt_out, s_tab,
                         warm, a.lam_out, &nc.solve, &nc.fail, nb);
     nc.calls += 1;
