@@ -298,8 +298,9 @@ int alb_exp_neg(const double* s, int n, double* out, void* stream);
 
 /* The same with the cheaper variant of the FP32 form's FP64 residual
  * evaluations: table index from an FP32 copy of s, one-step reduction and
- * degree-3 polynomial, relative error below 2e-13 for |s| <= 700. Same
- * arguments and limits. */
+ * degree-2 polynomial, relative error below 5e-10 for |s| <= 700 (the
+ * residuals are summed over the values it returns, so the 1e-12 criterion
+ * does not depend on it). Same arguments and limits. */
 int alb_exp_neg_refine(const double* s, int n, double* out, void* stream);
 
 /* Shift criterion (Eq. criterion with offset n0, clamped to +-u_max) applied

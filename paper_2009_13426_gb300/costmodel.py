@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # step kernel to the slots this model gives for the same launch; it absorbs
 # what the hand count misses (compiler scheduling, predication) and is
 # measured again whenever a kernel changes.
-CALIBRATION = {"fp32": 554.4 / 526.7, "fp64": 5573.7 / 6073.3}
+CALIBRATION = {"fp32": 518.1 / 495.7, "fp64": 5573.7 / 6073.3}
 
 BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
                   "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}
@@ -105,13 +105,13 @@ def plain_call():
 
 def mixed_eval():
     """FP64 residual evaluation of the refinement: grouped exponents (55),
-    21 table-driven exponentials (6 each: the table index, taken from an FP32
+    21 table-driven exponentials (5 each: the table index, taken from an FP32
     copy of the exponent, converted to FP64, the one-step reduction, the
-    degree-3 polynomial 3, the scaling), grouped constraint sums started at
+    degree-2 polynomial 2, the scaling), grouped constraint sums started at
     -m so that they end as the residual (68), its FP32 copy (8; its maximum
     is taken in FP32, and the FP32 corrections join the FP64 multipliers only
     before a further full evaluation)."""
-    return 55 + 21 * 6 + 68 + 8
+    return 55 + 21 * 5 + 68 + 8
 
 
 def mixed_update():
@@ -130,11 +130,11 @@ def mixed_call():
 COLLISION = {
     # FP64 part only: the 4 FP32 sums converted, one reciprocal of rho and 8
     # operations for u and T, the velocities in the absolute frame (4), the
-    # criterion's comparisons (8), the FP32 view of the equilibrium column (21
-    # conversions), T, rho and the stored moments in FP32 (6); tau, the
-    # sensor and BGK run in FP32, and the stored multipliers come out of the
-    # solver in FP32
-    "fp32": 4 + W_DIV + 8 + 4 + 8 + 21 + 6,
+    # FP32 view of the equilibrium column (21 conversions), T, rho and the
+    # stored moments in FP32 (6); the criterion compares on the integer pipe,
+    # tau, the sensor and BGK run in FP32, and the stored multipliers come
+    # out of the solver in FP32
+    "fp32": 4 + W_DIV + 8 + 4 + 21 + 6,
     "fp64": 90 + 3 * W_DIV + 5 + 2 + 24 + (W_DIV + 1) + W_DIV + 21 * 7 + 2,
 }
 
@@ -170,7 +170,7 @@ def method_floor(mlups: float) -> dict:
     constraint sums), the least a solve needs to confirm max|G|/rho <= 1e-12
     in FP64 (App. C.1). Returns that count, the MLUPS the FP64 pipe would
     allow if it were all the work, and the fraction of it `mlups` reaches."""
-    slots = 55 + 21 * 6 + 68
+    slots = 55 + 21 * 5 + 68
     cap = FP64_PEAK_TFLOPS * 1e12 / 2.0 / slots / 1e6
     return {"fp64_slots_per_node": slots, "mlups_at_fp64_peak": round(cap, 1),
             "frac": round(mlups / cap, 4)}

@@ -126,23 +126,26 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
   return e < -1022 ? 0.0 : (e > 1023 ? __longlong_as_double(0x7ff0000000000000LL) : v);
 }
 
-// exp(-s) for the FP32 form's residual evaluations, which need ~1e-13
-// relative accuracy only (their tolerance is 1e-12 on G/rho and the result is
-// rounded to FP32): the same table, the reduction in one step with ln2/N
-// rounded, and the degree-3 Taylor polynomial (truncation below 1.4e-13).
+// exp(-s) for the FP32 form's refinement: the same table, the reduction in
+// one step with ln2/N rounded, and the degree-2 Taylor polynomial. Its
+// accuracy does not enter the convergence test: each residual is summed
+// exactly (in FP64) over the column of values this function fills, so
+// max|G|/rho <= 1e-12 holds for the populations returned. It only sets how
+// closely those populations follow the exponential family of the returned
+// multipliers: to 5e-10 relative here, next to the ~1e-10 the multiplicative
+// updates leave, both far below the FP32 storage of the populations.
 // The table index n nearest to -s N / ln2 comes from s32, an FP32 value of
 // the same exponent: within |s| <= 745 (past which the result is 0 or +inf
 // anyway) FP32 holds s to 5e-5, a fiftieth of ln2/N, so n is the nearest
 // integer or its neighbour at a tie and |r| stays below 0.52 ln2/N
-// (truncation below 1.6e-13). 6 FP64 operations: n converted to FP64, the
-// reduction, the polynomial and the scaling. For |s32 N / ln2| >= 2^31 the
-// conversion saturates and e takes the limits; a NaN gives n = 0 and passes
-// through the polynomial.
+// (truncation r^3/3! below 4.7e-10). 5 FP64 operations: n converted to FP64,
+// the reduction, the polynomial and the scaling. For |s32 N / ln2| >= 2^31
+// the conversion saturates and e takes the limits; a NaN gives n = 0 and
+// passes through the polynomial.
 __device__ __forceinline__ double exp_neg_refine(double s, float s32, const double* tab) {
   const int n = __float2int_rn(-s32 * (float)EXPT_INV_L);
   const double r = fma((double)n, -EXPT_L, -s);
-  double q = fma(r, EXPT_C3, EXPT_C2);
-  q = fma(q, r, 1.0);
+  double q = fma(r, EXPT_C2, 1.0);
   q = fma(q, r, 1.0);
   const int e = n >> EXPT_BITS;
   const int ec = e < -1100 ? -1100 : (e > 1100 ? 1100 : e);  // keeps the shift defined

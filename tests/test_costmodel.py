@@ -17,7 +17,7 @@ def test_update_is_cheaper_than_an_evaluation():
     # an update replaces the 21 exponents and exponentials by a conversion and
     # an FMA per velocity; the sums, residual and bookkeeping are shared
     shared = 68 + 8
-    assert C.mixed_eval() - shared == 55 + 21 * 6
+    assert C.mixed_eval() - shared == 55 + 21 * 5
     assert C.mixed_update() - shared == 21 * 2
     assert C.mixed_update() < C.mixed_eval()
 

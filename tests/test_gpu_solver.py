@@ -1,12 +1,14 @@
 """The FP32 form's equilibrium solver and its FP64 exponential, through the C ABI.
 
 * alb_equilibrium with ALB_FP32_FORM (FP32 Newton refined with FP64
-  residuals) against the CPU oracle on 10^4 states: 1e-10 relative, the same
-  convergence decision, and few FP64 evaluations per state; after the
-  refinement's multiplicative updates the populations are still the
-  exponential of the returned multipliers to 1e-9.
+  residuals) against the CPU oracle on 10^4 states: 1e-9 relative (the
+  refinement's exponential and updates keep its populations within that of
+  the exponential family), the same convergence decision, constraint
+  residuals below the 1e-12 criterion, and few FP64 evaluations per state;
+  after the refinement's multiplicative updates the populations are still
+  the exponential of the returned multipliers to 1e-9.
 * alb_exp_neg (table-driven FP64 exponential, Tang's method) against CUDA's
-  own exp: a few ulp.
+  own exp: a few ulp; the refinement's cheaper variant within 5e-10.
 """
 import numpy as np
 import pytest
@@ -55,9 +57,12 @@ def test_mixed_solver_matches_oracle(alb):
         assert (ost == O.OK) == (st[k] == 0), (k, rho[k], ubx[k], uby[k], T[k], ost, st[k])
         if ost == O.OK:
             # Both stop at max|G|/rho <= 1e-12, the refinement as soon as it is met
-            # (near 1e-13), the oracle's Newton usually well below it; populations
-            # agree to the criterion's sensitivity, not to round-off.
-            np.testing.assert_allclose(feq[k], ofeq, rtol=1e-10, atol=2e-12 * rho[k])
+            # (near 1e-13), the oracle's Newton usually well below it. The
+            # refinement's populations follow the exponential family to the error
+            # of its exponential (below 5e-10, alb_exp_neg_refine) plus that of
+            # the multiplicative updates (about 1e-10): they agree with the
+            # oracle's to 1e-9, while both meet the criterion (next test).
+            np.testing.assert_allclose(feq[k], ofeq, rtol=1e-9, atol=2e-12 * rho[k])
     ok = st == 0
     # FP64 work: the refinement needs a few residual evaluations per state
     assert np.mean(evals[ok]) <= 4.0, np.mean(evals[ok])
@@ -120,10 +125,12 @@ def test_table_exponential_against_cuda_exp(alb):
 
 
 def test_refinement_exponential_within_its_bound(alb):
-    """The FP32 form's residual exponential: degree-3 Taylor polynomial on
-    |r| <= ln2/512 (remainder r^4/4! < 1.4e-13) and a one-step reduction
-    (error below 1e-14 for |s| < 700): relative error below 2e-13 against
-    CUDA's FP64 exp, and the same limits."""
+    """The FP32 form's refinement exponential: degree-2 Taylor polynomial on
+    |r| <= 0.52 ln2/256 (remainder r^3/3! < 4.7e-10, the table index taken
+    from an FP32 copy of s) and a one-step reduction (error below 3e-14 for
+    |s| < 700): relative error below 5e-10 against CUDA's FP64 exp, and the
+    same limits. The residuals it feeds are summed over its own values, so
+    the 1e-12 criterion does not depend on this bound."""
     rng = np.random.default_rng(9)
     s = np.concatenate([rng.uniform(-30, 60, 400000), rng.uniform(-690, 690, 100000),
                         np.arange(-64, 64) * np.log(2) / 32 + np.log(2) / 512,
@@ -135,8 +142,8 @@ def test_refinement_exponential_within_its_bound(alb):
     ref = torch.exp(-sd)
     torch.cuda.synchronize()
     rel = np.abs(out.cpu().numpy() - ref.cpu().numpy()) / ref.cpu().numpy()
-    assert rel.max() <= 2e-13, rel.max()
-    assert rel.max() > 4 * 2.0 ** -52  # it is the cheaper variant
+    assert rel.max() <= 5e-10, rel.max()
+    assert rel.max() > 1e-12  # it is the cheap variant
     _check_limits(alb.alb_exp_neg_refine)
     # a NaN exponent (its FP32 copy converts to table index 0) stays NaN
     t = _dev(np.array([np.nan, 1.0]))
@@ -144,7 +151,7 @@ def test_refinement_exponential_within_its_bound(alb):
     alb.alb_exp_neg_refine(t, 2, o)
     torch.cuda.synchronize()
     o = o.cpu().numpy()
-    assert np.isnan(o[0]) and abs(o[1] - np.exp(-1.0)) <= 2e-13 * np.exp(-1.0), o
+    assert np.isnan(o[0]) and abs(o[1] - np.exp(-1.0)) <= 5e-10 * np.exp(-1.0), o
 
 
 def test_refinement_keeps_the_exponential_form(alb):
