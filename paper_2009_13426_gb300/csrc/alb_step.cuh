@@ -467,36 +467,30 @@ __device__ __forceinline__ void tile_step(const StepArgs<P>& a, int x0, int y0, 
     k = (size_t)y * pr.nx + x;
     code = a.nxt_in[k];
     const int Upx = lat_ux(code), Upy = lat_uy(code);
-    // Three passes, so that each kind of load is in flight for all 21
-    // velocities at once (a pull's load written straight to shared memory
-    // would wait for the previous velocity's): the senders' lattice codes,
-    // the populations of the senders in this node's lattice, then the
-    // shared-memory column and the queue of missing pulls.
-    size_t ks[Q];
-    {
-      int sc[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        bool gh = false;
-        const int rx = resolve(x - XI_X(i) - Upx, pr.nx, pr.bcx, &gh);
-        const int ry = resolve(y - XI_Y(i) - Upy, pr.ny, pr.bcy, &gh);
-        ks[i] = (size_t)ry * pr.nx + rx;
-        sc[i] = gh ? -1 : (int)a.lat_in[ks[i]];  // a ghost sender is always rebuilt
-      }
-#pragma unroll
-      for (int i = 0; i < Q; ++i) own |= (sc[i] == code ? 1u : 0u) << i;
-    }
-    // populations are read once and written once per step: streaming
+    // All loads first, so that they are in flight together (a pull's load
+    // written straight to shared memory would wait for the previous
+    // velocity's): for every velocity the sender's lattice code and its two
+    // populations, whether or not the sender turns out to live in this node's
+    // lattice (the index is inside the grid even for a ghost: resolve clamps
+    // it). Then the populations of the senders in this lattice go to the
+    // shared-memory column; the others are dropped and queued for a rebuild.
+    // Populations are read once and written once per step: streaming
     // (evict-first) loads and stores keep L2 for the lattice codes and the
-    // threads' stack
+    // threads' stack.
+    int sc[Q];
     P v[2 * Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      if (own & (1u << i)) {
-        v[i] = __ldcs(&a.pop_in[i * ps + ks[i]]);
-        v[Q + i] = __ldcs(&a.pop_in[(Q + i) * ps + ks[i]]);
-      }
+      bool gh = false;
+      const int rx = resolve(x - XI_X(i) - Upx, pr.nx, pr.bcx, &gh);
+      const int ry = resolve(y - XI_Y(i) - Upy, pr.ny, pr.bcy, &gh);
+      const size_t ks = (size_t)ry * pr.nx + rx;
+      sc[i] = gh ? -1 : (int)a.lat_in[ks];  // a ghost sender is always rebuilt
+      v[i] = __ldcs(&a.pop_in[i * ps + ks]);
+      v[Q + i] = __ldcs(&a.pop_in[(Q + i) * ps + ks]);
     }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) own |= (sc[i] == code ? 1u : 0u) << i;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (own & (1u << i)) {
