@@ -60,11 +60,11 @@ from paper_2009_13426_gb300 import costmodel, flows  # noqa: E402
 METRIC = "adaptive D2Q21 MLUPS, FP32 form vs FP64 plain at stated error; serve p50/p99"
 # DRAM bytes (read + write) per node update of step_kernel<float>, from one
 # ncu capture of the 1024^2 case of the same flow (dram__bytes_read.sum +
-# dram__bytes_write.sum = 226.1 + 366.3 MB per launch for 1,048,576 nodes,
+# dram__bytes_write.sum = 226.9 + 370.5 MB per launch for 1,048,576 nodes,
 # mean of the first 3 launches, kinetic sensor on); the traffic
 # grows in proportion to the nodes, so a 4096^2 launch moves 16,777,216 x
 # this. Measured on the current kernel.
-TRAFFIC_BYTES_PER_NODE_FP32 = 565.0
+TRAFFIC_BYTES_PER_NODE_FP32 = 569.7
 UNIT = "MLUPS"
 NU = 1e-5
 # The kinetic sensor (Sec. IV.A.2) is on in every timed flow: without it the
@@ -835,7 +835,7 @@ def run_ours(args, world, rank, local):
                      "frac": round(achieved_tflops / costmodel.FP64_PEAK_TFLOPS, 4),
                      "traffic": round(TRAFFIC_BYTES_PER_NODE_FP32 * N),
                      "traffic_note": "ncu DRAM bytes per node on the 1024^2 case x nodes: "
-                                     "1.35 x the 420 algorithmic bytes, the excess being "
+                                     "1.36 x the 420 algorithmic bytes, the excess being "
                                      "the threads' stack (spills, call frames) leaving L2",
                      "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "kernel": "step_kernel<float>",

@@ -2,8 +2,10 @@
 
 The step is bound by the FP64 pipe, not by HBM: on GB300 the FP64 rate is
 1/62 of the FP32 rate. Its FP64 arithmetic is counted in issue slots: one
-slot per FP64 lane operation (DFMA, DADD, DMUL, DMNMX, DSETP, conversions to
-or from FP64), and for CUDA's FP64 routines their measured cost in slots
+slot per FP64 lane operation (DFMA, DADD, DMUL, DMNMX, DSETP, hardware
+conversions to or from FP64; the FP32 form's hot conversions are assembled
+on the integer pipe instead and cost no slot), and for CUDA's FP64 routines
+their measured cost in slots
 (throughput microbenchmark on GB300, independent chains, loop overhead
 removed): exp 18.2, divide/reciprocal 9.2, square root 10, log 20. The counts
 come from the structure of the kernel's unrolled code over the D2Q21 velocity
@@ -33,7 +35,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 1.2586
 # step kernel to the slots this model gives for the same launch; it absorbs
 # what the hand count misses (compiler scheduling, predication) and is
 # measured again whenever a kernel changes.
-CALIBRATION = {"fp32": 518.1 / 495.7, "fp64": 5573.7 / 6073.3}
+CALIBRATION = {"fp32": 405.4 / 385.2, "fp64": 5573.7 / 6073.3}
 
 BYTES_PER_NODE = {"fp32": 42 * 4 * 2 + 4 * 4 + 4 + 8 * 4 * 2,
                   "fp64": 42 * 8 * 2 + 4 * 8 + 4 + 8 * 8 * 2}
@@ -105,36 +107,39 @@ def plain_call():
 
 def mixed_eval():
     """FP64 residual evaluation of the refinement: grouped exponents (55),
-    21 table-driven exponentials (5 each: the table index, taken from an FP32
-    copy of the exponent, converted to FP64, the one-step reduction, the
-    degree-2 polynomial 2, the scaling), grouped constraint sums started at
-    -m so that they end as the residual (68), its FP32 copy (8; its maximum
-    is taken in FP32, and the FP32 corrections join the FP64 multipliers only
-    before a further full evaluation)."""
-    return 55 + 21 * 5 + 68 + 8
+    21 table-driven exponentials (4 each: the one-step reduction, the
+    degree-2 polynomial 2, the scaling; the table index comes from an FP32
+    copy of the exponent and reaches FP64 through the integer pipe), grouped
+    constraint sums started at -m so that they end as the residual (68). Its
+    FP32 copy is rounded on the integer pipe (its maximum is taken in FP32,
+    and the FP32 corrections join the FP64 multipliers only before a further
+    full evaluation)."""
+    return 55 + 21 * 4 + 68
 
 
 def mixed_update():
     """Multiplicative FP64 update of the refinement after a small step: per
-    velocity the FP32 factor exp(-d) - 1 converted to FP64 and one FMA
-    (21 x 2; the exponent changes d are FP32), grouped constraint sums
-    started at -m (68), the residual's FP32 copy (8)."""
-    return 21 * 2 + 68 + 8
+    velocity one FMA with the FP32 factor exp(-d) - 1 (21; the exponent
+    changes d are FP32, the factor reaches FP64 through the integer pipe),
+    grouped constraint sums started at -m (68); the residual's FP32 copy is
+    rounded on the integer pipe."""
+    return 21 + 68
 
 
 def mixed_call():
-    """Targets and conversions of the inputs and the FP32 multipliers."""
-    return 8 + 8 + 3
+    """Targets (the inputs and the FP32 multipliers change precision on the
+    integer pipe)."""
+    return 8
 
 
 COLLISION = {
-    # FP64 part only: the 4 FP32 sums converted, one reciprocal of rho and 8
-    # operations for u and T, the velocities in the absolute frame (4), the
-    # FP32 view of the equilibrium column (21 conversions), T, rho and the
-    # stored moments in FP32 (6); the criterion compares on the integer pipe,
-    # tau, the sensor and BGK run in FP32, and the stored multipliers come
-    # out of the solver in FP32
-    "fp32": 4 + W_DIV + 8 + 4 + 21 + 6,
+    # FP64 part only: one reciprocal of rho and 8 operations for u and T,
+    # the velocities in the absolute frame (2); the FP32 sums, the FP32 view
+    # of the equilibrium column, T, rho and the stored moments change
+    # precision on the integer pipe, the criterion compares there too, tau,
+    # the sensor and BGK run in FP32, and the stored multipliers come out of
+    # the solver in FP32
+    "fp32": W_DIV + 8 + 2,
     "fp64": 90 + 3 * W_DIV + 5 + 2 + 24 + (W_DIV + 1) + W_DIV + 21 * 7 + 2,
 }
 
@@ -170,7 +175,7 @@ def method_floor(mlups: float) -> dict:
     constraint sums), the least a solve needs to confirm max|G|/rho <= 1e-12
     in FP64 (App. C.1). Returns that count, the MLUPS the FP64 pipe would
     allow if it were all the work, and the fraction of it `mlups` reaches."""
-    slots = 55 + 21 * 5 + 68
+    slots = 55 + 21 * 4 + 68
     cap = FP64_PEAK_TFLOPS * 1e12 / 2.0 / slots / 1e6
     return {"fp64_slots_per_node": slots, "mlups_at_fp64_peak": round(cap, 1),
             "frac": round(mlups / cap, 4)}

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "alb_cvt.cuh"
+
 namespace alb {
 
 constexpr int Q = 21;   // D2Q21
@@ -41,6 +43,16 @@ __host__ __device__ __forceinline__ constexpr int PM(int k, int i) {
 __host__ __device__ __forceinline__ int lat_code(int ux, int uy) { return (ux + 3) + 7 * (uy + 3); }
 __host__ __device__ __forceinline__ int lat_ux(int c) { return c % 7 - 3; }
 __host__ __device__ __forceinline__ int lat_uy(int c) { return c / 7 - 3; }
+
+// A double in the population precision P: FP32 rounded on the integer pipe
+// (cvt_f32_rn, the hardware rounding for every value of FP32's normal range),
+// FP64 unchanged.
+template <typename P>
+__device__ __forceinline__ P to_p(double v);
+template <>
+__device__ __forceinline__ float to_p<float>(double v) { return cvt_f32_rn(v); }
+template <>
+__device__ __forceinline__ double to_p<double>(double v) { return v; }
 
 // Physical and numerical parameters of one flow, passed by value.
 struct Params {
@@ -158,7 +170,7 @@ __device__ __forceinline__ int select_shift(double u, double n0, int umax) {
 // in the population precision P.
 template <typename P>
 __device__ __forceinline__ P sensor_alpha(const Params& pr, P eps) {
-  if (!(eps > (P)pr.seps[0])) return (P)1;
+  if (!(eps > to_p<P>(pr.seps[0]))) return (P)1;
   const P l = log10(eps);
 #pragma unroll
   for (int k = 0; k < 3; ++k)

@@ -144,7 +144,7 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
 // passes through the polynomial.
 __device__ __forceinline__ double exp_neg_refine(double s, float s32, const double* tab) {
   const int n = __float2int_rn(-s32 * (float)EXPT_INV_L);
-  const double r = fma((double)n, -EXPT_L, -s);
+  const double r = fma(cvt_f64(n), -EXPT_L, -s);
   double q = fma(r, EXPT_C2, 1.0);
   q = fma(q, r, 1.0);
   const int e = n >> EXPT_BITS;
@@ -390,7 +390,7 @@ struct PassMul64 : SumsG64 {
   __device__ __forceinline__ double upd(int i, float d) const {
     const float e = d * fmaf(d, fmaf(d, -1.0f / 6.0f, 0.5f), -1.0f);
     double* q = col + (size_t)i * stride;
-    const double p = fma(*q, (double)e, *q);
+    const double p = fma(*q, cvt_f64(e), *q);
     *q = p;
     return p;
   }
@@ -640,7 +640,7 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
   float acc[NM];   // corrections since then
 #pragma unroll
   for (int k = 0; k < NM; ++k) {
-    lam[k] = (double)lam32[k];
+    lam[k] = cvt_f64(lam32[k]);
     acc[k] = 0.0f;
     lam_out32[k] = lam32[k];
   }
@@ -661,7 +661,7 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
       if (r > 0) {
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
-          lam[k] += (double)acc[k];
+          lam[k] += cvt_f64(acc[k]);
           acc[k] = 0.0f;
         }
       }
@@ -679,7 +679,7 @@ static __device__ __noinline__ int refine_fp64(double ubx, double uby, double T,
     float g32[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
-      g32[k] = (float)G[k];
+      g32[k] = cvt_f32_rn(G[k]);
       finite = finite && isfinite(g32[k]);
       gmax = fmaxf(gmax, fabsf(g32[k]));
     }
@@ -1062,14 +1062,15 @@ __device__ __forceinline__ int equilibrium_mixed(double ubx, double uby, double 
   Fact32 fc;
   int it32 = 0, ev = 0;
   int st = NEWTON_SINGULAR;
+  const float ubx32 = cvt_f32_rn(ubx), uby32 = cvt_f32_rn(uby), T32 = cvt_f32_rn(T);
   if (warm) {
 #pragma unroll
     for (int k = 0; k < NM; ++k) l32[k] = warm[k];
-    st = newton_fp32((float)ubx, (float)uby, (float)T, 30, true, l32, fc, &it32);
+    st = newton_fp32(ubx32, uby32, T32, 30, true, l32, fc, &it32);
     cnt->fp32_iters += it32;
   }
   if (st != NEWTON_OK) {
-    st = newton_fp32((float)ubx, (float)uby, (float)T, 30, false, l32, fc, &it32);
+    st = newton_fp32(ubx32, uby32, T32, 30, false, l32, fc, &it32);
     cnt->fp32_iters += it32;
   }
   if (st == NEWTON_OK) {

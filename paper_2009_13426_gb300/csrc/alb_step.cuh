@@ -97,7 +97,7 @@ struct Acc<float> {
       c += (v - t) + s;
     s = t;
   }
-  __device__ __forceinline__ double val() const { return (double)(s + c); }
+  __device__ __forceinline__ double val() const { return cvt_f64(s + c); }
   __device__ __forceinline__ float valf() const { return s + c; }
 };
 
@@ -216,7 +216,7 @@ __device__ __forceinline__ const P* eq_in_precision(double* eq) {
   if constexpr (std::is_same<P, float>::value) {
     float* v = reinterpret_cast<float*>(eq);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[2 * i * B] = (float)eq[i * B];
+    for (int i = 0; i < Q; ++i) v[2 * i * B] = cvt_f32_rn(eq[i * B]);
     return v;
   } else {
     return eq;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
     uby = ajy.val() / rho;
     T = (ae.val() - rho * (ubx * ubx + uby * uby)) / (2.0 * rho * pr.cv);
   }
-  const double ux = ubx + (double)Ux, uy = uby + (double)Uy;
+  const double ux = ubx + cvt_f64(Ux), uy = uby + cvt_f64(Uy);
   // next lattice: Eq. criterion, or overlapping ranges chosen by history or
   // by the neighbours' current lattices nb[0..7]
   const bool by_nb = order_key(pr.overlap) > 0 && pr.rule == 1 && nb;
@@ -351,10 +351,10 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
   if (ns == NEWTON_OK) {
     // f^eq = rho p, g^eq = (2 Cv - D) T f^eq and tau = 1/2 + nu/T in the
     // population precision (in the FP32 form from the FP64 equilibrium)
-    const P Tp = (P)T;
-    const P gp = ((P)2 * (P)pr.cv - (P)2) * Tp;
-    P tau = (P)0.5 + (P)pr.nu / Tp;
-    const P rp = (P)rho;
+    const P Tp = to_p<P>(T);
+    const P gp = ((P)2 * to_p<P>(pr.cv) - (P)2) * Tp;
+    P tau = (P)0.5 + to_p<P>(pr.nu) / Tp;
+    const P rp = to_p<P>(rho);
     const P* eqv = eq_in_precision<P, B>(cl.eq);
     constexpr int es = eq_stride<P, B>();
     if (pr.sensor) {
@@ -386,10 +386,10 @@ __device__ __forceinline__ void collide_store(const Params& pr, const Columns<P,
 #pragma unroll
     for (int i = 0; i < NPLANES; ++i) pop_out[i * ps + k] = st[i * B];
   }
-  mom_out[k] = (P)rho;
-  mom_out[ps + k] = (P)ux;
-  mom_out[2 * ps + k] = (P)uy;
-  mom_out[3 * ps + k] = (P)T;
+  mom_out[k] = to_p<P>(rho);
+  mom_out[ps + k] = to_p<P>(ux);
+  mom_out[2 * ps + k] = to_p<P>(uy);
+  mom_out[3 * ps + k] = to_p<P>(T);
   lat_out[k] = (uint8_t)code;
   nxt_out[k] = (uint8_t)code2;
 }
