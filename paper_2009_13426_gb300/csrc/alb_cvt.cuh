@@ -15,8 +15,8 @@
 #pragma once
 
 #include <stdint.h>
-#ifndef __CUDACC__
 #include <string.h>
+#ifndef __CUDACC__
 #define ALB_CVT_FN inline
 #else
 #define ALB_CVT_FN __host__ __device__ __forceinline__
