@@ -57,3 +57,15 @@ def test_method_floor_is_one_fp64_evaluation():
     cap = 152 * 2 * 2.07e9 / f["fp64_slots_per_node"] / 1e6
     assert f["mlups_at_fp64_peak"] == pytest.approx(cap, rel=1e-3)
     assert f["frac"] == pytest.approx(500.0 / cap, rel=1e-3)
+
+
+def test_fp32_calibration_is_the_profiled_capture():
+    # the FP32 form's factor is ncu's FP64-pipe thread instructions per node
+    # (405.4, 1024^2 shear layer, first three launches) over this model's
+    # slots for the counters of the same launches: 1.0973 solves and full
+    # evaluations, 1.1581 multiplicative updates, 0.1875 rebuilt pulls
+    st = {"newton_iterations": 0, "newton_calls": 1.0973, "fp64_evaluations": 1.0973,
+          "fp64_updates": 1.1581, "reconstructions": 0.1875, "node_updates": 1.0}
+    raw = C.fp64_slots(st, "fp32") / C.CALIBRATION["fp32"]
+    assert raw == pytest.approx(385.2, abs=0.05)
+    assert C.fp64_slots(st, "fp32") == pytest.approx(405.4, abs=0.05)
