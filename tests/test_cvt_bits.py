@@ -138,3 +138,35 @@ def test_integer_conversions_match_ieee(tmp_path):
     assert int(counts["i2d"]) > 2_000_000 and int(counts["bad"]) == 0
     # the flushed range was reached (both directions have inputs there)
     assert int(counts["flushed"]) > 1000
+
+
+# Mistakes planted in copies of the header: ties rounded away from zero, the
+# exponent threshold of the flushed range off by one, the int32 exponent bias
+# off by one, the FP32 -> FP64 bias off by one, the fraction shifted by one
+# bit. Each must make the comparison fail.
+PLANTED = [
+    ("((r == 0x10000000u) & (m & 1u))", "(r == 0x10000000u)"),
+    ("b = e <= 0 ? 0u : b;", "b = e < 0 ? 0u : b;"),
+    ("(1054 - lz)", "(1053 - lz)"),
+    ("e + 896u", "e + 895u"),
+    ("(x >> 12)", "(x >> 11)"),
+]
+
+
+def test_planted_mistakes_fail(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    header = open(os.path.join(HEADER_DIR, "alb_cvt.cuh")).read()
+    (tmp_path / "cvt_check.cpp").write_text(DRIVER)
+    for k, (good, bad) in enumerate(PLANTED):
+        assert header.count(good) == 1, good
+        d = tmp_path / ("m%d" % k)
+        d.mkdir()
+        (d / "alb_cvt.cuh").write_text(header.replace(good, bad))
+        exe = d / "cvt_check"
+        subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", str(d),
+                        str(tmp_path / "cvt_check.cpp"), "-o", str(exe)],
+                       check=True, capture_output=True, text=True)
+        r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+        assert r.returncode != 0, ("planted mistake not caught", bad)
