@@ -138,10 +138,10 @@ __device__ __forceinline__ double exp_neg(double s, const double* tab) {
 // the same exponent: within |s| <= 745 (past which the result is 0 or +inf
 // anyway) FP32 holds s to 5e-5, a fiftieth of ln2/N, so n is the nearest
 // integer or its neighbour at a tie and |r| stays below 0.52 ln2/N
-// (truncation r^3/3! below 4.7e-10). 5 FP64 operations: n converted to FP64,
-// the reduction, the polynomial and the scaling. For |s32 N / ln2| >= 2^31
-// the conversion saturates and e takes the limits; a NaN gives n = 0 and
-// passes through the polynomial.
+// (truncation r^3/3! below 4.7e-10). 4 FP64 operations: the reduction, the
+// polynomial and the scaling (n reaches FP64 exactly on the integer pipe).
+// For |s32 N / ln2| >= 2^31 the float-to-int rounding saturates and e takes
+// the limits; a NaN gives n = 0 and passes through the polynomial.
 __device__ __forceinline__ double exp_neg_refine(double s, float s32, const double* tab) {
   const int n = __float2int_rn(-s32 * (float)EXPT_INV_L);
   const double r = fma(cvt_f64(n), -EXPT_L, -s);
@@ -380,8 +380,9 @@ struct PassG64 {
 // vector); for |d_i| <= 1e-3 (checked by the caller) the update's factor has
 // a relative error of about 1e-10, so the column stays an exponential-family
 // member to that level, while the sums that decide convergence are exact FP64
-// sums of the column. Two FP64 operations per velocity instead of an
-// exponent and an exponential.
+// sums of the column. One FP64 operation per velocity (the factor reaches
+// FP64 exactly on the integer pipe) instead of an exponent and an
+// exponential.
 struct PassMul64 : SumsG64 {
   double* col;
   int stride;

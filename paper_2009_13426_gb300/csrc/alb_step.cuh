@@ -209,8 +209,8 @@ __device__ __noinline__ int rebuild_pull(const Params pr, const P* __restrict__ 
 // population precision. In the FP32 form every value is rounded to FP32 once,
 // in place, into the first word of its slot (the FP64 value is not read
 // again), so that the sensor, the BGK update and the App. E term read the
-// same float and the FP64 pipe converts each value once; element i is then
-// at [i * eq_stride<P, B>()].
+// same float; the rounding runs on the integer pipe (cvt_f32_rn), not the
+// FP64 pipe. Element i is then at [i * eq_stride<P, B>()].
 template <typename P, int B>
 __device__ __forceinline__ const P* eq_in_precision(double* eq) {
   if constexpr (std::is_same<P, float>::value) {
